@@ -1,0 +1,393 @@
+"""Benchmark of the fused FPC-LBM step on GB300 (one JSON line on stdout).
+
+Workload (default): the 3D differentially heated cubic cavity, 256^3 nodes, D3Q27 flow + D3Q15
+energy, FP32 populations, Ra = 1e6, Pr = 0.71, Ma = 0.1 (hot -x, cold +x, adiabatic elsewhere,
+gravity along z).  One step = one fused pull-stream + collide launch of both lattices; the wall
+Nusselt reduction (FP64) runs on both heated walls once per timed block.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank advances its own independent cavity (an ensemble member, no
+data exchange) and the aggregate node updates are divided by the slowest rank's time.
+``--impl reference`` times the FP64 CPU oracle (the method's plain restatement) on the host cores
+for the same workload, a bounded sample of nodes per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("MLUPS and % HBM roofline per lattice/precision on 1 GB300; adjoint step time vs "
+          "forward")
+WORKLOAD = dict(lattice="d3q27", nx=256, ny=256, nz=256, Ra=1e6, Pr=0.71, Ma=0.1, precision="fp32")
+KERNEL_SOURCES = ["lbm_common.cuh", "lattices.cuh", "step_d3q27.cuh", "step3d_f32.cu", "kernels.h"]
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def reduce_max(value: float, world: int) -> float:
+    """Max of a per-rank value over all ranks (identity on one rank)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------------------------
+# Clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        ids = [v.strip() for v in vis.split(",")] if vis else []
+        self.gpu = ids[local_rank] if local_rank < len(ids) else str(local_rank)
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# Measured peaks and committed ncu traffic
+# ---------------------------------------------------------------------------------------------
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2504_09041_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it still
+    describes the current kernel source (same source hash), else None."""
+    p = os.path.join(ROOT, "profiles", "step_d3q27_f32_cavity.md")
+    try:
+        text = open(p).read()
+    except OSError:
+        return None
+    m_t = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    m_h = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    if not m_t or not m_h or m_h.group(1) != kernel_source_hash():
+        return None
+    return float(m_t.group(1))
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+    from paper_2504_09041_gb300 import lbm as L
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    w = WORKLOAD
+    walls = L.Walls.cavity(3)
+    walls.seed = 1000 + rank        # each rank: its own ensemble member
+    walls.perturb = 1e-3
+    with torch.cuda.stream(stream):
+        lat = L.Lattice(w["lattice"], w["nx"], w["ny"], w["nz"], w["Ra"], w["Pr"], w["Ma"],
+                        walls=walls, precision=w["precision"], stream=stream)
+    n = lat.n
+    info = lat.info()
+    bpn = info.bytes_per_node_update
+
+    # warm-up
+    lat.step(args.warmup)
+    lat.nusselt(0)
+    lat.sync()
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        ev[0].record(stream)
+        lat.step(args.steps)
+        ev[1].record(stream)
+        nu_hot = L.lbm_nusselt(lat.h, 0)
+        nu_cold = L.lbm_nusselt(lat.h, 1)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    lat.sync()
+    t_total = ev[0].elapsed_time(ev[2]) / 1e3
+    t_steps = ev[0].elapsed_time(ev[1]) / 1e3
+    t_max = reduce_max(t_total, world)
+    launches = args.steps + 2
+
+    # end to end through the C ABI with host buffers: upload a state from pinned host memory,
+    # run the steps, read back the wall Nusselt numbers and the temperature field.
+    state_host = torch.empty(info.state_bytes, dtype=torch.uint8).pin_memory()
+    T_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    L.lbm_get_state(lat.h, state_host.numpy())
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L.lbm_set_state(lat.h, state_host.numpy())
+    L.lbm_step(lat.h, args.steps)
+    L.lbm_nusselt(lat.h, 0)
+    L.lbm_nusselt(lat.h, 1)
+    L.lbm_fields(lat.h, None, None, None, None, T_host.data_ptr(), 0)
+    torch.cuda.synchronize()
+    t_e2e = reduce_max(time.perf_counter() - t0, world)
+
+    forms = []
+    if world == 1 and not args.no_forms:
+        forms = measure_forms(L, torch, stream, args)
+
+    clk = clocks.summary()
+    lat.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+
+    mlups = n * args.steps * world / t_max / 1e6
+    step_s = t_steps / args.steps
+    achieved = bpn * n / step_s / 1e9
+    peak, peak_kind = hbm_peak()
+    traffic = committed_traffic()
+    e2e = n * args.steps * world / t_e2e / 1e6
+    line = {
+        "metric": METRIC,
+        "value": round(mlups, 2),
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_max / args.steps * 1e3, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded initial temperature perturbation +-1e-3 of the cavity at rest)",
+        "config": {"workload": "3D differentially heated cubic cavity, D3Q27 flow + D3Q15 energy, "
+                               "FP32 populations, FP64 Nusselt reduction",
+                   "nx": w["nx"], "ny": w["ny"], "nz": w["nz"], "Ra": w["Ra"], "Pr": w["Pr"],
+                   "Ma": w["Ma"], "nodes_per_gpu": n, "bytes_per_node_update": bpn,
+                   "nusselt_every": args.steps,
+                   "l2": "inputs larger than L2 (2.8 GB read and 2.8 GB written per step)",
+                   "parallelism": "independent cavity per GPU (ensemble member)" if world > 1
+                   else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_kind": peak_kind, "kernel": "step_d3q27_kernel<StoreF32>",
+                     "launch_ms": round(step_s * 1e3, 4)},
+        "e2e": {"value": round(e2e, 2), "unit": "MLUPS",
+                "h2d_bytes_per_step": info.state_bytes / args.steps,
+                "d2h_bytes_per_step": (8 * n + 80) / args.steps,
+                "job": "set_state from pinned host + K steps + 2 wall Nusselt + T field to host"},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "nusselt": {"hot_mean": nu_hot[0], "cold_mean": nu_cold[0], "steps_done": info.steps},
+    }
+    if forms:
+        line["per_form"] = forms
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
+    return line
+
+
+def measure_forms(L, torch, stream, args):
+    """MLUPS and HBM fraction of the other lattice / precision forms on the same GPU."""
+    out = []
+    peak, _ = hbm_peak()
+    cases = [("d3q27", 256, 256, 256, "fp64", L.Walls.cavity(3), 1e6, 20),
+             ("d3q27", 256, 256, 256, "fp16s", L.Walls.cavity(3), 1e6, 50),
+             ("d2q9", 1024, 512, 1, "fp64", L.Walls.rayleigh_benard(seed=1), 1e8, 200),
+             ("d2q9", 1024, 512, 1, "fp32", L.Walls.rayleigh_benard(seed=1), 1e8, 400),
+             ("d2q9", 1024, 512, 1, "fp16s", L.Walls.rayleigh_benard(seed=1), 1e8, 400)]
+    for lat_name, nx, ny, nz, prec, walls, Ra, k in cases:
+        lat = L.Lattice(lat_name, nx, ny, nz, Ra, 0.71, 0.1, walls=walls, precision=prec, stream=stream)
+        lat.step(5)
+        lat.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lat.sync()
+        s = e0.elapsed_time(e1) / 1e3 / k
+        bpn = lat.info().bytes_per_node_update
+        gbs = bpn * lat.n / s / 1e9
+        out.append({"lattice": "D3Q27+D3Q15" if lat_name == "d3q27" else "D2Q9+D2Q9",
+                    "precision": prec, "box": [nx, ny, nz], "mlups": round(lat.n / s / 1e6, 1),
+                    "ms_per_step": round(s * 1e3, 4), "gbs": round(gbs, 1),
+                    "hbm_frac": round(gbs / peak, 4), "steps": k})
+        lat.close()
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU side: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------------------------
+def oracle_sample(seconds: float):
+    """Time the oracle on slabs of the 256^3 cavity (full x-y planes, a few z layers) until about
+    `seconds` of wall time has been spent; returns (MLUPS, threads, description)."""
+    from oracle import oracle as O
+    w = WORKLOAD
+    nz = 4
+    ora = O.Oracle(3, w["nx"], w["ny"], nz, bc=O.cavity_bc(3), Ra=w["Ra"], Pr=w["Pr"], Ma=w["Ma"])
+    # the rates and g beta of the full 256^3 cavity (L = 256 along x, as in the slab)
+    nodes, t_sum, reps = 0, 0.0, 0
+    while t_sum < seconds or reps == 0:
+        t0 = time.perf_counter()
+        ora.update_box(0, w["nx"], 0, w["ny"], 0, nz)
+        t_sum += time.perf_counter() - t0
+        nodes += w["nx"] * w["ny"] * nz
+        reps += 1
+    desc = (f"{reps} node-update sweeps of a {w['nx']}x{w['ny']}x{nz} slab of the 256^3 cavity "
+            f"({nodes} node updates, {t_sum:.1f} s)")
+    return nodes / t_sum / 1e6, O.threads(), desc
+
+
+def cpu_baseline(seconds: float = 15.0):
+    mlups, cores, desc = oracle_sample(seconds)
+    return {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": desc}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    from oracle import oracle as O
+    w = WORKLOAD
+    nz = 2
+    ora = O.Oracle(3, w["nx"], w["ny"], nz, bc=O.cavity_bc(3), Ra=w["Ra"], Pr=w["Pr"], Ma=w["Ma"])
+    for _ in range(args.warmup):
+        ora.update_box(0, w["nx"], 0, w["ny"], 0, nz)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ora.update_box(0, w["nx"], 0, w["ny"], 0, nz)
+    t = time.perf_counter() - t0
+    nodes = w["nx"] * w["ny"] * nz * args.steps
+    mlups = nodes / t / 1e6
+    sample = (f"each step updates a {w['nx']}x{w['ny']}x{nz} slab of the 256^3 cavity "
+              f"({w['nx'] * w['ny'] * nz} nodes) with the FP64 oracle")
+    return {"metric": METRIC, "value": round(mlups, 4), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "3D differentially heated cubic cavity, D3Q27 flow + D3Q15 "
+                                   "energy (oracle sample of the 256^3 box)",
+                       "nx": w["nx"], "ny": w["ny"], "nz": w["nz"], "Ra": w["Ra"], "Pr": w["Pr"],
+                       "Ma": w["Ma"]},
+            "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": O.threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--nx", type=int, default=None, help="override the box (profiling cases)")
+    ap.add_argument("--ny", type=int, default=None)
+    ap.add_argument("--nz", type=int, default=None)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    for k in ("nx", "ny", "nz"):
+        if getattr(args, k) is not None:
+            WORKLOAD[k] = getattr(args, k)
+    line = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * lbm.h -- C ABI of liblbm.so: the GB300 (sm_103a) hot path of the Fokker-Planck central-moment
+ * lattice Boltzmann method for thermal convection (Schupbach & Premnath, arXiv 2504.09041).
+ *
+ * One time step advances two coupled lattices at every node: the flow populations f (D2Q9,
+ * App. A; or D3Q27, Sec. 4.1-4.3) relaxed toward the FP central-moment attractors with the
+ * renormalized diffusion tensor and the Boussinesq source, and the energy populations g (D2Q9,
+ * App. B; or D3Q15, App. C) relaxed toward their own (option-A) attractors.  The step is one fused
+ * pull-stream + collide kernel launch (Eqs. LBMsteps-collide / LBMsteps-stream).
+ *
+ * Conventions used by every entry point:
+ *  - Return value: LBM_OK (0) or one of the lbm_status codes; nothing traps, no exception crosses
+ *    the ABI.  lbm_last_error(h) describes the most recent failure on h (or of lbm_create when
+ *    h is NULL).
+ *  - Node index i = x + nx * (y + ny * z), x fastest.  Population arrays are [q][nz][ny][nx] in
+ *    the paper's link order (D2Q9 Eqs. ex, ey; D3Q27 Sec. 4.2; D3Q15 Sec. 4.4).
+ *  - Faces are numbered 0..5 = -x, +x, -y, +y, -z, +z.  2D boxes have nz = 1 and ignore the z faces.
+ *  - The library owns its device buffers (allocated through lbm_set_allocator's hook, cudaMalloc by
+ *    default).  Caller buffers are only read or written during the call that receives them.
+ *  - Work is queued on the handle's stream (lbm_set_stream; the legacy default stream otherwise).
+ *    Calls that return data to the host synchronize that stream.
+ *  - Handles are not thread-safe; use one handle per thread or serialize calls.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_s* lbm_handle;
+
+enum lbm_status {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,     /* invalid argument (bad size, face, key, rate outside (0, 2), ...) */
+    LBM_ENOMEM = 2,     /* the device allocator returned NULL */
+    LBM_ECUDA = 3,      /* a CUDA call failed; lbm_last_error has the CUDA message */
+    LBM_EDIVERGED = 4,  /* a node saw a non-finite or non-positive density or a non-finite T */
+    LBM_ENOTSUP = 6     /* valid request that this build does not support */
+};
+
+/* Lattice pair, OR-ed with one storage precision. */
+enum lbm_lattice { LBM_D2Q9_D2Q9 = 1, LBM_D3Q27_D3Q15 = 2 };
+enum lbm_prec {
+    LBM_FP64 = 0x000,   /* populations stored and relaxed in FP64 */
+    LBM_FP32 = 0x100,   /* populations stored and relaxed in FP32 */
+    LBM_FP16S = 0x200   /* FP16 storage of f_a - w_a and g_a - w_a T_o, FP32 moment algebra */
+};
+enum lbm_face_bc {
+    LBM_PERIODIC = 0,        /* both faces of an axis must be periodic, or neither */
+    LBM_WALL_ADIABATIC = 1,  /* half-way bounce-back of f (no slip) and of g (zero heat flux) */
+    LBM_WALL_FIXED_T = 2     /* bounce-back of f, anti-bounce-back of g at T_wall (Sec. 5.1) */
+};
+
+typedef struct {
+    int face[6];                /* lbm_face_bc of -x, +x, -y, +y, -z, +z */
+    double T_wall[6];           /* wall temperature of LBM_WALL_FIXED_T faces */
+    double T_init;              /* initial uniform temperature */
+    double T_ref;               /* T_o of the Boussinesq force F = g beta (T - T_o) (Sec. 5.1) */
+    int gravity_axis;           /* axis of the buoyancy force: 1 (y) in 2D, 2 (z) in 3D */
+    unsigned long long seed;    /* splitmix64 seed of the initial temperature perturbation */
+    double perturb;             /* T_init += perturb * (2 U_i - 1), U_i uniform in [0, 1) */
+} lbm_bc;
+
+typedef struct {
+    int lattice, precision;     /* lbm_lattice and lbm_prec values */
+    int nx, ny, nz, q_f, q_g;
+    double L;                   /* characteristic length: nodes across the fixed-T faces' axis */
+    double dT;                  /* T_H - T_C over the fixed-T faces (1 if fewer than two differ) */
+    double U, nu, alpha, gbeta; /* U_o = Ma/sqrt(3); nu = U L sqrt(Pr/Ra); alpha = nu/Pr;
+                                   g beta = U^2/(L dT)   (Sec. 5.1, Sec. 6) */
+    double T_ref;
+    double om_f[27], om_g[15];  /* relaxation rates in use (see lbm_set_omegas) */
+    long long steps;            /* time steps taken since creation */
+    double bytes_per_node_update; /* algorithmic HBM bytes per node and step: 2 (q_f + q_g) size */
+    size_t state_bytes;         /* size of an lbm_get_state checkpoint */
+} lbm_info_t;
+
+/*
+ * Device allocator hook (process-wide).  alloc(bytes, ctx) returns device memory or NULL;
+ * free(ptr, ctx) releases it.  NULL functions restore cudaMalloc / cudaFree.  A handle keeps the
+ * hook it was created with.  Returns LBM_OK.
+ */
+typedef void* (*lbm_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*lbm_free_fn)(void* ptr, void* ctx);
+LBM_API int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void* ctx);
+
+/*
+ * Create a box of nx * ny * nz nodes (nz = 1 for LBM_D2Q9_D2Q9) for the cavity problems of
+ * Sec. 5.1 / 5.2: Rayleigh number Ra, Prandtl number Pr and Mach number Ma = sqrt(3) U_o
+ * (Sec. 6) fix nu, alpha and g beta (see lbm_info_t) and the rates
+ *   nu = c_s^2 (1/omega - 1/2)        on the shear moments of f (App. A: omega_4, omega_5),
+ *   alpha = c_s^2 (1/omega - 1/2)     on the first-order moments of g (App. B, App. C),
+ * every other rate 1.0 (App. A, B, C).  The populations start at the rest attractors at density 1
+ * and temperature T_init (+ the seeded perturbation).
+ * Errors: LBM_EINVAL (sizes < 1, nz != 1 in 2D, more than 2^31 - 1 nodes, Ra/Pr/Ma not positive
+ * and finite, bad face kinds, one-sided periodic axis, bad gravity axis), LBM_ENOMEM, LBM_ECUDA.
+ * On success *out owns the handle; release it with lbm_destroy.
+ */
+LBM_API int lbm_create(int lattice, int nx, int ny, int nz, double Ra, double Pr, double Ma,
+               const lbm_bc* bc, lbm_handle* out);
+LBM_API int lbm_destroy(lbm_handle h);
+
+/* Queue all further work of h on the CUDA stream `stream` (a cudaStream_t; NULL = legacy). */
+LBM_API int lbm_set_stream(lbm_handle h, void* stream);
+
+/*
+ * Replace the relaxation rates.  om_f: n_f = q_f rates of the flow collision; om_g: n_g = q_g
+ * rates of the energy collision (either pointer may be NULL to keep the current rates).
+ *  - D2Q9 f: omega_0..omega_8 of App. A Step 3 (omega_3 on kappa_2s, omega_4 on kappa_2d).
+ *  - D2Q9 g: omega_0..omega_8 of App. B Step 3 (omega_3, omega_4 on the eta_2s, eta_2d pair).
+ *  - D3Q15 g: omega_0..omega_14 of App. C Step 3.
+ *  - D3Q27 f: one rate per entry of the central-moment vector of Sec. 4.2, except slot 7 which
+ *    relaxes the trace kappa_200 + kappa_020 + kappa_002 and slots 8, 9 which relax the deviators
+ *    kappa_200 - kappa_020 and kappa_200 - kappa_002.
+ * Every rate must lie in (0, 2) (App. A).  Errors: LBM_EINVAL.
+ */
+LBM_API int lbm_set_omegas(lbm_handle h, const double* om_f, int n_f, const double* om_g, int n_g);
+
+/* Set a scalar parameter: "gbeta", "T_ref", "omega_nu", "omega_alpha", "omega_bulk".
+ * Errors: LBM_EINVAL for an unknown key or a rate outside (0, 2). */
+LBM_API int lbm_set_param(lbm_handle h, const char* key, double value);
+LBM_API int lbm_info(lbm_handle h, lbm_info_t* out);
+
+/*
+ * Advance n >= 0 time steps (asynchronous on the handle's stream): per step one fused launch that
+ * pulls the post-collision populations along every link with the wall rules of Sec. 5.1, forms
+ * T = sum g, F = g beta (T - T_o) along gravity, rho = sum f, rho u = sum f e + F/2 (App. A Step 7),
+ * and relaxes f and g in central-moment space (App. A/B/C Steps 1-5).
+ * Errors: LBM_EINVAL (n < 0), LBM_ECUDA (launch failure).  Divergence is reported by lbm_sync.
+ */
+LBM_API int lbm_step(lbm_handle h, long n);
+
+/* Wait for the handle's queued work and report divergence: LBM_EDIVERGED if any node of any step
+ * since the last lbm_sync saw a non-finite or non-positive density or a non-finite temperature. */
+LBM_API int lbm_sync(lbm_handle h);
+
+/*
+ * Macroscopic fields of the streamed populations at the current time (App. A Step 7 and App. B/C
+ * Step 7): rho, u (with the half-force term) and T, FP64, n = nx*ny*nz values each.  Pointers are
+ * device pointers when device_ptrs != 0, else host pointers; any pointer may be NULL.
+ */
+LBM_API int lbm_fields(lbm_handle h, double* rho, double* ux, double* uy, double* uz, double* T,
+               int device_ptrs);
+
+/*
+ * Wall Nusselt number on a fixed-temperature face (Sec. 5.1): at every wall node,
+ *   dT/dn = -8/3 T_w + 3 T_1 - 1/3 T_2   (wall at 0, node layers at 1/2 and 3/2, n into the fluid)
+ *   Nu = -s (L / dT) dT/dn,  s = +1 if the face's T_wall >= T_ref, else -1,
+ * reduced in FP64 to the mean over the face nodes and the max / min with their tangential node
+ * index j (x faces: j = y + ny z; y faces: j = x + nx z; z faces: j = x + nx y; its location is
+ * (j + 1/2) / N along that axis).  Any output pointer may be NULL.
+ * Errors: LBM_EINVAL (face not a fixed-T wall of this box, or fewer than 2 node layers).
+ */
+LBM_API int lbm_nusselt(lbm_handle h, int face, double* mean, double* nu_max, double* nu_min, int* j_max,
+                int* j_min);
+/* The local Nu of every node of that face (n = number of face nodes), host or device pointer. */
+LBM_API int lbm_nusselt_profile(lbm_handle h, int face, double* nu, long n, int device_ptrs);
+
+/* Per-node wall temperature of a fixed-T face (n = face nodes, tangential order as above, host
+ * pointer); T_w = NULL returns the face to its uniform T_wall.  Errors: LBM_EINVAL. */
+LBM_API int lbm_set_wall_profile(lbm_handle h, int face, const double* T_w, long n);
+
+/*
+ * The stored state is the post-collision populations of the last step (before streaming).
+ * lbm_get_populations / lbm_set_populations convert it from / to FP64 arrays f[q_f][n],
+ * g[q_g][n] (device pointers when device_ptrs != 0).  With FP16S storage the values are
+ * shift + deviation, formed in FP64.
+ */
+LBM_API int lbm_get_populations(lbm_handle h, double* f, double* g, int device_ptrs);
+LBM_API int lbm_set_populations(lbm_handle h, const double* f, const double* g, int device_ptrs);
+
+/* Checkpoint / restart in the storage format: bytes must equal lbm_info's state_bytes; buf is a
+ * host buffer.  lbm_set_state also restores the step counter.  Errors: LBM_EINVAL on a size,
+ * lattice, precision or shape mismatch. */
+LBM_API int lbm_get_state(lbm_handle h, void* buf, size_t bytes);
+LBM_API int lbm_set_state(lbm_handle h, const void* buf, size_t bytes);
+
+LBM_API const char* lbm_last_error(lbm_handle h);
+LBM_API const char* lbm_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,574 @@
+// api.cu -- the C ABI of liblbm.so (declared in include/lbm.h).
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/lbm.h"
+#include "kernels.h"
+
+namespace {
+
+void* default_alloc(size_t bytes, void*)
+{
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+void default_free(void* p, void*) { cudaFree(p); }
+
+lbm_alloc_fn g_alloc = default_alloc;
+lbm_free_fn g_free = default_free;
+void* g_ctx = nullptr;
+thread_local std::string g_create_error;
+
+constexpr unsigned long long kStateMagic = 0x46504c424d535431ULL;  // "FPLBMST1"
+constexpr size_t kStateHeader = 64;
+
+}  // namespace
+
+struct lbm_s {
+    int lattice = 0, prec = 0, dim = 0, nx = 0, ny = 0, nz = 0, qf = 0, qg = 0;
+    lbm::Geometry geo{};
+    lbm::HostCoeffs hc{};
+    lbm_bc bc{};
+    double L = 0, dT = 1, U = 0, nu = 0, alpha = 0;
+    void* f[2] = {nullptr, nullptr};
+    void* g[2] = {nullptr, nullptr};
+    int cur = 0;
+    double* profile[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double* nu_profile = nullptr;   // max face nodes
+    double* nu_scratch = nullptr;   // block partials
+    double* nu_result = nullptr;    // 5 doubles
+    unsigned* ticket = nullptr;
+    unsigned* status = nullptr;
+    cudaStream_t stream = nullptr;
+    long long steps = 0;
+    std::string err;
+    lbm_alloc_fn alloc = nullptr;
+    lbm_free_fn dealloc = nullptr;
+    void* actx = nullptr;
+};
+
+namespace {
+
+int fail(lbm_s* h, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+#define LBM_CK(h, expr)                                                                          \
+    do {                                                                                         \
+        cudaError_t e_ = (expr);                                                                 \
+        if (e_ != cudaSuccess) return fail(h, LBM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+void* dev_alloc(lbm_s* h, size_t bytes)
+{
+    return h->alloc(bytes, h->actx);
+}
+void dev_free(lbm_s* h, void* p)
+{
+    if (p) h->dealloc(p, h->actx);
+}
+
+void release(lbm_s* h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (int k = 0; k < 2; ++k) {
+        dev_free(h, h->f[k]);
+        dev_free(h, h->g[k]);
+    }
+    for (int k = 0; k < 6; ++k) dev_free(h, h->profile[k]);
+    dev_free(h, h->nu_profile);
+    dev_free(h, h->nu_scratch);
+    dev_free(h, h->nu_result);
+    dev_free(h, h->ticket);
+    dev_free(h, h->status);
+    delete h;
+}
+
+bool rate_ok(double w) { return std::isfinite(w) && w > 0.0 && w < 2.0; }
+
+long face_nodes(const lbm_s* h, int face)
+{
+    const int ax = face / 2;
+    if (ax == 0) return (long)h->ny * h->nz;
+    if (ax == 1) return (long)h->nx * h->nz;
+    return (long)h->nx * h->ny;
+}
+
+size_t pop_bytes(const lbm_s* h)
+{
+    return (size_t)(h->qf + h->qg) * (size_t)h->geo.n * lbm::storage_bytes(h->prec);
+}
+
+// Default rates (App. A, B, C): shear / diffusivity rates from nu / alpha, every other rate 1.
+void default_rates(lbm_s* h, double om_nu, double om_alpha, double om_bulk)
+{
+    for (int a = 0; a < 27; ++a) h->hc.om_f[a] = 1.0;
+    for (int b = 0; b < 15; ++b) h->hc.om_g[b] = 1.0;
+    if (h->dim == 2) {
+        h->hc.om_f[3] = om_bulk;
+        h->hc.om_f[4] = h->hc.om_f[5] = om_nu;
+        h->hc.om_g[1] = h->hc.om_g[2] = om_alpha;
+    } else {
+        h->hc.om_f[4] = h->hc.om_f[5] = h->hc.om_f[6] = om_nu;
+        h->hc.om_f[7] = om_bulk;
+        h->hc.om_f[8] = h->hc.om_f[9] = om_nu;
+        h->hc.om_g[1] = h->hc.om_g[2] = h->hc.om_g[3] = om_alpha;
+    }
+}
+
+// Device temporary of n doubles for host <-> device staging.
+struct Tmp {
+    lbm_s* h;
+    double* p = nullptr;
+    Tmp(lbm_s* hh, size_t n) : h(hh) { p = (double*)dev_alloc(h, n * sizeof(double)); }
+    ~Tmp()
+    {
+        if (p) {
+            cudaStreamSynchronize(h->stream);
+            dev_free(h, p);
+        }
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void* ctx)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) return fail(nullptr, LBM_EINVAL, "allocator: give both functions or neither");
+    g_alloc = alloc ? alloc : default_alloc;
+    g_free = free_fn ? free_fn : default_free;
+    g_ctx = alloc ? ctx : nullptr;
+    return LBM_OK;
+}
+
+const char* lbm_status_string(int s)
+{
+    switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "out of device memory";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_EDIVERGED: return "simulation diverged";
+    case LBM_ENOTSUP: return "not supported";
+    }
+    return "unknown status";
+}
+
+const char* lbm_last_error(lbm_handle h)
+{
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int lbm_create(int lattice, int nx, int ny, int nz, double Ra, double Pr, double Ma,
+               const lbm_bc* bc, lbm_handle* out)
+{
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    const int lat = lattice & 0xff;
+    const int prec_code = lattice & ~0xff;
+    if (lat != LBM_D2Q9_D2Q9 && lat != LBM_D3Q27_D3Q15)
+        return fail(nullptr, LBM_EINVAL, "unknown lattice %d", lat);
+    int prec;
+    if (prec_code == LBM_FP64) prec = lbm::kF64;
+    else if (prec_code == LBM_FP32) prec = lbm::kF32;
+    else if (prec_code == LBM_FP16S) prec = lbm::kF16S;
+    else return fail(nullptr, LBM_EINVAL, "unknown precision flag 0x%x", prec_code);
+    const int dim = lat == LBM_D2Q9_D2Q9 ? 2 : 3;
+    if (dim == 2 && nz == 0) nz = 1;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "box %d x %d x %d is empty", nx, ny, nz);
+    if (dim == 2 && nz != 1) return fail(nullptr, LBM_EINVAL, "2D boxes need nz = 1");
+    if ((long long)nx * ny * nz > INT_MAX) return fail(nullptr, LBM_EINVAL, "more than 2^31 - 1 nodes");
+    if (nz > 65535 || (ny + 1) / 2 > 65535) return fail(nullptr, LBM_EINVAL, "box too tall for the launch grid");
+    if (!(std::isfinite(Ra) && Ra > 0) || !(std::isfinite(Pr) && Pr > 0) || !(std::isfinite(Ma) && Ma > 0))
+        return fail(nullptr, LBM_EINVAL, "Ra, Pr and Ma must be positive and finite");
+    if (!bc) return fail(nullptr, LBM_EINVAL, "bc is NULL");
+    for (int f = 0; f < 6; ++f)
+        if (bc->face[f] < LBM_PERIODIC || bc->face[f] > LBM_WALL_FIXED_T)
+            return fail(nullptr, LBM_EINVAL, "face %d: unknown kind %d", f, bc->face[f]);
+    for (int ax = 0; ax < dim; ++ax)
+        if ((bc->face[2 * ax] == LBM_PERIODIC) != (bc->face[2 * ax + 1] == LBM_PERIODIC))
+            return fail(nullptr, LBM_EINVAL, "axis %d is periodic on one face only", ax);
+    if (bc->gravity_axis < 0 || bc->gravity_axis >= dim)
+        return fail(nullptr, LBM_EINVAL, "gravity axis %d out of range", bc->gravity_axis);
+
+    lbm_s* h = new lbm_s;
+    h->alloc = g_alloc;
+    h->dealloc = g_free;
+    h->actx = g_ctx;
+    h->lattice = lat;
+    h->prec = prec;
+    h->dim = dim;
+    h->nx = nx;
+    h->ny = ny;
+    h->nz = nz;
+    h->qf = dim == 2 ? 9 : 27;
+    h->qg = dim == 2 ? 9 : 15;
+    h->bc = *bc;
+    lbm::Geometry& g = h->geo;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.nxy = nx * ny;
+    g.n = nx * ny * nz;
+    for (int f = 0; f < 6; ++f) {
+        g.kind[f] = (dim == 2 && f >= 4) ? LBM_PERIODIC : bc->face[f];
+        g.T_wall[f] = bc->T_wall[f];
+        g.profile[f] = nullptr;
+    }
+
+    // Problem parameters (Sec. 5.1, Sec. 6): L across the fixed-T faces, U = Ma / sqrt(3),
+    // g beta dT L = U^2, nu = U L sqrt(Pr / Ra), alpha = nu / Pr.
+    const int ext[3] = {nx, ny, nz};
+    h->L = nx;
+    double tmin = INFINITY, tmax = -INFINITY;
+    int nfixed = 0;
+    for (int f = 2 * dim - 1; f >= 0; --f)
+        if (g.kind[f] == LBM_WALL_FIXED_T) h->L = ext[f / 2];
+    for (int f = 0; f < 2 * dim; ++f)
+        if (g.kind[f] == LBM_WALL_FIXED_T) {
+            ++nfixed;
+            tmin = fmin(tmin, bc->T_wall[f]);
+            tmax = fmax(tmax, bc->T_wall[f]);
+        }
+    h->dT = (nfixed >= 2 && tmax > tmin) ? tmax - tmin : 1.0;
+    h->U = Ma / std::sqrt(3.0);
+    h->nu = h->U * h->L * std::sqrt(Pr / Ra);
+    h->alpha = h->nu / Pr;
+    h->hc.gbeta = h->U * h->U / (h->L * h->dT);
+    h->hc.T_ref = bc->T_ref;
+    h->hc.gaxis = bc->gravity_axis;
+    const double om_nu = 1.0 / (3.0 * h->nu + 0.5);
+    const double om_alpha = 1.0 / (3.0 * h->alpha + 0.5);
+    default_rates(h, om_nu, om_alpha, 1.0);
+
+    // Device memory.
+    const size_t sb = lbm::storage_bytes(prec);
+    long max_face = 0;
+    for (int f = 0; f < 2 * dim; ++f) max_face = std::max(max_face, face_nodes(h, f));
+    for (int k = 0; k < 2; ++k) {
+        h->f[k] = dev_alloc(h, (size_t)h->qf * g.n * sb);
+        h->g[k] = dev_alloc(h, (size_t)h->qg * g.n * sb);
+    }
+    h->nu_profile = (double*)dev_alloc(h, sizeof(double) * max_face);
+    h->nu_scratch = (double*)dev_alloc(h, sizeof(double) * lbm::nusselt_scratch_doubles(max_face));
+    h->nu_result = (double*)dev_alloc(h, sizeof(double) * 8);
+    h->ticket = (unsigned*)dev_alloc(h, sizeof(unsigned) * 4);
+    h->status = (unsigned*)dev_alloc(h, sizeof(unsigned) * 4);
+    if (!h->f[0] || !h->f[1] || !h->g[0] || !h->g[1] || !h->nu_profile || !h->nu_scratch ||
+        !h->nu_result || !h->ticket || !h->status) {
+        fail(nullptr, LBM_ENOMEM, "device allocation failed for a %d x %d x %d box", nx, ny, nz);
+        release(h);
+        return LBM_ENOMEM;
+    }
+    cudaError_t e = cudaMemsetAsync(h->ticket, 0, sizeof(unsigned) * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(unsigned) * 4, h->stream);
+    if (e == cudaSuccess)
+        e = lbm::launch_init(dim, prec, h->f[0], h->g[0], g, bc->T_init, bc->T_ref, bc->seed,
+                             bc->perturb, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        fail(nullptr, LBM_ECUDA, "initialisation: %s", cudaGetErrorString(e));
+        release(h);
+        return LBM_ECUDA;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_handle h)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+    release(h);
+    return LBM_OK;
+}
+
+int lbm_set_stream(lbm_handle h, void* stream)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+    h->stream = (cudaStream_t)stream;
+    return LBM_OK;
+}
+
+int lbm_set_omegas(lbm_handle h, const double* om_f, int n_f, const double* om_g, int n_g)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+    if (om_f && n_f != h->qf) return fail(h, LBM_EINVAL, "expected %d flow rates, got %d", h->qf, n_f);
+    if (om_g && n_g != h->qg) return fail(h, LBM_EINVAL, "expected %d energy rates, got %d", h->qg, n_g);
+    for (int a = 0; om_f && a < n_f; ++a)
+        if (!rate_ok(om_f[a])) return fail(h, LBM_EINVAL, "flow rate %d = %g outside (0, 2)", a, om_f[a]);
+    for (int b = 0; om_g && b < n_g; ++b)
+        if (!rate_ok(om_g[b])) return fail(h, LBM_EINVAL, "energy rate %d = %g outside (0, 2)", b, om_g[b]);
+    for (int a = 0; om_f && a < n_f; ++a) h->hc.om_f[a] = om_f[a];
+    for (int b = 0; om_g && b < n_g; ++b) h->hc.om_g[b] = om_g[b];
+    return LBM_OK;
+}
+
+int lbm_set_param(lbm_handle h, const char* key, double v)
+{
+    if (!h || !key) return fail(h, LBM_EINVAL, "handle or key is NULL");
+    const std::string k(key);
+    if (k == "gbeta" || k == "T_ref") {
+        if (!std::isfinite(v)) return fail(h, LBM_EINVAL, "%s must be finite", key);
+        (k == "gbeta" ? h->hc.gbeta : h->hc.T_ref) = v;
+        return LBM_OK;
+    }
+    if (!rate_ok(v)) return fail(h, LBM_EINVAL, "%s = %g outside (0, 2)", key, v);
+    if (k == "omega_nu") {
+        if (h->dim == 2) h->hc.om_f[4] = h->hc.om_f[5] = v;
+        else h->hc.om_f[4] = h->hc.om_f[5] = h->hc.om_f[6] = h->hc.om_f[8] = h->hc.om_f[9] = v;
+    } else if (k == "omega_alpha") {
+        h->hc.om_g[1] = h->hc.om_g[2] = v;
+        if (h->dim == 3) h->hc.om_g[3] = v;
+    } else if (k == "omega_bulk") {
+        h->hc.om_f[h->dim == 2 ? 3 : 7] = v;
+    } else {
+        return fail(h, LBM_EINVAL, "unknown parameter '%s'", key);
+    }
+    return LBM_OK;
+}
+
+int lbm_info(lbm_handle h, lbm_info_t* o)
+{
+    if (!h || !o) return fail(h, LBM_EINVAL, "handle or output is NULL");
+    memset(o, 0, sizeof *o);
+    o->lattice = h->lattice;
+    o->precision = h->prec == lbm::kF64 ? LBM_FP64 : (h->prec == lbm::kF32 ? LBM_FP32 : LBM_FP16S);
+    o->nx = h->nx;
+    o->ny = h->ny;
+    o->nz = h->nz;
+    o->q_f = h->qf;
+    o->q_g = h->qg;
+    o->L = h->L;
+    o->dT = h->dT;
+    o->U = h->U;
+    o->nu = h->nu;
+    o->alpha = h->alpha;
+    o->gbeta = h->hc.gbeta;
+    o->T_ref = h->hc.T_ref;
+    for (int a = 0; a < 27; ++a) o->om_f[a] = a < h->qf ? h->hc.om_f[a] : 0.0;
+    for (int b = 0; b < 15; ++b) o->om_g[b] = b < h->qg ? h->hc.om_g[b] : 0.0;
+    o->steps = h->steps;
+    o->bytes_per_node_update = 2.0 * (h->qf + h->qg) * (double)lbm::storage_bytes(h->prec);
+    o->state_bytes = kStateHeader + pop_bytes(h);
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle h, long n)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+    if (n < 0) return fail(h, LBM_EINVAL, "negative step count %ld", n);
+    for (long t = 0; t < n; ++t) {
+        const int c = h->cur;
+        LBM_CK(h, lbm::launch_step(h->dim, h->prec, h->f[c], h->g[c], h->f[1 - c], h->g[1 - c],
+                                   h->geo, h->hc, h->status, h->stream));
+        h->cur = 1 - c;
+        ++h->steps;
+    }
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_handle h)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+    unsigned st = 0;
+    LBM_CK(h, cudaMemcpyAsync(&st, h->status, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CK(h, cudaStreamSynchronize(h->stream));
+    if (st) {
+        LBM_CK(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+        return fail(h, LBM_EDIVERGED, "non-finite or non-positive density or temperature by step %lld",
+                    h->steps);
+    }
+    return LBM_OK;
+}
+
+int lbm_fields(lbm_handle h, double* rho, double* ux, double* uy, double* uz, double* T,
+               int device_ptrs)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+    const size_t n = (size_t)h->geo.n;
+    double* outs[5] = {rho, ux, uy, uz, T};
+    const bool direct = device_ptrs && rho && ux && uy && uz && T;
+    if (direct) {
+        LBM_CK(h, lbm::launch_fields(h->dim, h->prec, h->f[h->cur], h->g[h->cur], h->geo, h->hc, rho,
+                                     ux, uy, uz, T, h->stream));
+        return LBM_OK;
+    }
+    Tmp tmp(h, 5 * n);
+    if (!tmp.p) return fail(h, LBM_ENOMEM, "no device memory for the field staging buffer");
+    LBM_CK(h, lbm::launch_fields(h->dim, h->prec, h->f[h->cur], h->g[h->cur], h->geo, h->hc, tmp.p,
+                                 tmp.p + n, tmp.p + 2 * n, tmp.p + 3 * n, tmp.p + 4 * n, h->stream));
+    for (int k = 0; k < 5; ++k)
+        if (outs[k])
+            LBM_CK(h, cudaMemcpyAsync(outs[k], tmp.p + k * n, n * sizeof(double),
+                                      device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                      h->stream));
+    LBM_CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+static int nusselt_common(lbm_s* h, int face)
+{
+    if (face < 0 || face >= 2 * h->dim) return fail(h, LBM_EINVAL, "face %d is not a face of this box", face);
+    if (h->geo.kind[face] != LBM_WALL_FIXED_T) return fail(h, LBM_EINVAL, "face %d is not a fixed-temperature wall", face);
+    const int ext[3] = {h->nx, h->ny, h->nz};
+    if (ext[face / 2] < 2) return fail(h, LBM_EINVAL, "fewer than two node layers normal to face %d", face);
+    const double s = h->geo.T_wall[face] >= h->hc.T_ref ? 1.0 : -1.0;
+    LBM_CK(h, lbm::launch_nusselt(h->dim, h->prec, h->f[h->cur], h->g[h->cur], h->geo, h->hc, face,
+                                  -s * h->L / h->dT, h->nu_profile, h->nu_scratch, h->ticket,
+                                  h->nu_result, h->stream));
+    return LBM_OK;
+}
+
+int lbm_nusselt(lbm_handle h, int face, double* mean, double* nu_max, double* nu_min, int* j_max,
+                int* j_min)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+    int rc = nusselt_common(h, face);
+    if (rc) return rc;
+    double r[5];
+    LBM_CK(h, cudaMemcpyAsync(r, h->nu_result, sizeof r, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CK(h, cudaStreamSynchronize(h->stream));
+    const long n = face_nodes(h, face);
+    if (mean) *mean = r[0] / (double)n;
+    if (nu_max) *nu_max = r[1];
+    if (j_max) *j_max = (int)r[2];
+    if (nu_min) *nu_min = r[3];
+    if (j_min) *j_min = (int)r[4];
+    return LBM_OK;
+}
+
+int lbm_nusselt_profile(lbm_handle h, int face, double* nu, long n, int device_ptrs)
+{
+    if (!h || !nu) return fail(h, LBM_EINVAL, "handle or output is NULL");
+    int rc = nusselt_common(h, face);
+    if (rc) return rc;
+    if (n != face_nodes(h, face)) return fail(h, LBM_EINVAL, "face %d has %ld nodes, not %ld", face, face_nodes(h, face), n);
+    LBM_CK(h, cudaMemcpyAsync(nu, h->nu_profile, n * sizeof(double),
+                              device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    LBM_CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_set_wall_profile(lbm_handle h, int face, const double* T_w, long n)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+    if (face < 0 || face >= 2 * h->dim || h->geo.kind[face] != LBM_WALL_FIXED_T)
+        return fail(h, LBM_EINVAL, "face %d is not a fixed-temperature wall", face);
+    if (!T_w) {
+        LBM_CK(h, cudaStreamSynchronize(h->stream));
+        dev_free(h, h->profile[face]);
+        h->profile[face] = nullptr;
+        h->geo.profile[face] = nullptr;
+        return LBM_OK;
+    }
+    if (n != face_nodes(h, face)) return fail(h, LBM_EINVAL, "face %d has %ld nodes, not %ld", face, face_nodes(h, face), n);
+    for (long k = 0; k < n; ++k)
+        if (!std::isfinite(T_w[k])) return fail(h, LBM_EINVAL, "wall temperature %ld is not finite", k);
+    if (!h->profile[face]) {
+        h->profile[face] = (double*)dev_alloc(h, n * sizeof(double));
+        if (!h->profile[face]) return fail(h, LBM_ENOMEM, "no device memory for the wall profile");
+    }
+    LBM_CK(h, cudaMemcpyAsync(h->profile[face], T_w, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    LBM_CK(h, cudaStreamSynchronize(h->stream));
+    h->geo.profile[face] = h->profile[face];
+    return LBM_OK;
+}
+
+int lbm_get_populations(lbm_handle h, double* f, double* g, int device_ptrs)
+{
+    if (!h || !f || !g) return fail(h, LBM_EINVAL, "handle or output is NULL");
+    const size_t n = (size_t)h->geo.n;
+    if (device_ptrs) {
+        LBM_CK(h, lbm::launch_get_pops(h->dim, h->prec, h->f[h->cur], h->g[h->cur], h->geo, h->hc.T_ref,
+                                       f, g, h->stream));
+        return LBM_OK;
+    }
+    Tmp tmp(h, (h->qf + h->qg) * n);
+    if (!tmp.p) return fail(h, LBM_ENOMEM, "no device memory for the staging buffer");
+    LBM_CK(h, lbm::launch_get_pops(h->dim, h->prec, h->f[h->cur], h->g[h->cur], h->geo, h->hc.T_ref,
+                                   tmp.p, tmp.p + h->qf * n, h->stream));
+    LBM_CK(h, cudaMemcpyAsync(f, tmp.p, h->qf * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LBM_CK(h, cudaMemcpyAsync(g, tmp.p + h->qf * n, h->qg * n * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
+    LBM_CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_handle h, const double* f, const double* g, int device_ptrs)
+{
+    if (!h || !f || !g) return fail(h, LBM_EINVAL, "handle or input is NULL");
+    const size_t n = (size_t)h->geo.n;
+    if (device_ptrs) {
+        LBM_CK(h, lbm::launch_set_pops(h->dim, h->prec, h->f[h->cur], h->g[h->cur], h->geo, h->hc.T_ref,
+                                       f, g, h->stream));
+        return LBM_OK;
+    }
+    Tmp tmp(h, (h->qf + h->qg) * n);
+    if (!tmp.p) return fail(h, LBM_ENOMEM, "no device memory for the staging buffer");
+    LBM_CK(h, cudaMemcpyAsync(tmp.p, f, h->qf * n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    LBM_CK(h, cudaMemcpyAsync(tmp.p + h->qf * n, g, h->qg * n * sizeof(double), cudaMemcpyHostToDevice,
+                              h->stream));
+    LBM_CK(h, lbm::launch_set_pops(h->dim, h->prec, h->f[h->cur], h->g[h->cur], h->geo, h->hc.T_ref,
+                                   tmp.p, tmp.p + h->qf * n, h->stream));
+    LBM_CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_get_state(lbm_handle h, void* buf, size_t bytes)
+{
+    if (!h || !buf) return fail(h, LBM_EINVAL, "handle or buffer is NULL");
+    if (bytes != kStateHeader + pop_bytes(h)) return fail(h, LBM_EINVAL, "state needs %zu bytes, got %zu", kStateHeader + pop_bytes(h), bytes);
+    unsigned long long hdr[8] = {kStateMagic, (unsigned long long)h->lattice, (unsigned long long)h->prec,
+                                 (unsigned long long)h->nx, (unsigned long long)h->ny,
+                                 (unsigned long long)h->nz, (unsigned long long)h->steps, 0ULL};
+    memcpy(buf, hdr, sizeof hdr);
+    char* p = (char*)buf + kStateHeader;
+    const size_t fb = (size_t)h->qf * h->geo.n * lbm::storage_bytes(h->prec);
+    const size_t gb = (size_t)h->qg * h->geo.n * lbm::storage_bytes(h->prec);
+    LBM_CK(h, cudaMemcpyAsync(p, h->f[h->cur], fb, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CK(h, cudaMemcpyAsync(p + fb, h->g[h->cur], gb, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_handle h, const void* buf, size_t bytes)
+{
+    if (!h || !buf) return fail(h, LBM_EINVAL, "handle or buffer is NULL");
+    if (bytes != kStateHeader + pop_bytes(h)) return fail(h, LBM_EINVAL, "state needs %zu bytes, got %zu", kStateHeader + pop_bytes(h), bytes);
+    unsigned long long hdr[8];
+    memcpy(hdr, buf, sizeof hdr);
+    if (hdr[0] != kStateMagic || hdr[1] != (unsigned long long)h->lattice ||
+        hdr[2] != (unsigned long long)h->prec || hdr[3] != (unsigned long long)h->nx ||
+        hdr[4] != (unsigned long long)h->ny || hdr[5] != (unsigned long long)h->nz)
+        return fail(h, LBM_EINVAL, "checkpoint does not match this box (lattice, precision or shape)");
+    const char* p = (const char*)buf + kStateHeader;
+    const size_t fb = (size_t)h->qf * h->geo.n * lbm::storage_bytes(h->prec);
+    const size_t gb = (size_t)h->qg * h->geo.n * lbm::storage_bytes(h->prec);
+    LBM_CK(h, cudaMemcpyAsync(h->f[h->cur], p, fb, cudaMemcpyHostToDevice, h->stream));
+    LBM_CK(h, cudaMemcpyAsync(h->g[h->cur], p + fb, gb, cudaMemcpyHostToDevice, h->stream));
+    LBM_CK(h, cudaStreamSynchronize(h->stream));
+    h->steps = (long long)hdr[6];
+    return LBM_OK;
+}
+
+}  // extern "C"

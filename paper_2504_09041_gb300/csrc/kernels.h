@@ -1,0 +1,88 @@
+// kernels.h -- host-side launchers of the CUDA kernels (internal to liblbm.so).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "lbm_common.cuh"
+
+namespace lbm {
+
+enum Prec { kF64 = 0, kF32 = 1, kF16S = 2 };
+
+// Relaxation rates and coupling in double precision; converted to the kernel's register type.
+struct HostCoeffs {
+    double om_f[27];
+    double om_g[15];
+    double gbeta, T_ref;
+    int gaxis;
+};
+
+size_t storage_bytes(int prec);
+
+cudaError_t launch_step(int dim, int prec, const void* fin, const void* gin, void* fout, void* gout,
+                        const Geometry& geo, const HostCoeffs& hc, unsigned* status, cudaStream_t st);
+cudaError_t launch_step_d2q9(int prec, const void* fin, const void* gin, void* fout, void* gout,
+                             const Geometry& geo, const HostCoeffs& hc, unsigned* status,
+                             cudaStream_t st);
+cudaError_t launch_step_d3q27_f64(const void* fin, const void* gin, void* fout, void* gout,
+                                  const Geometry& geo, const HostCoeffs& hc, unsigned* status,
+                                  cudaStream_t st);
+cudaError_t launch_step_d3q27_f32(const void* fin, const void* gin, void* fout, void* gout,
+                                  const Geometry& geo, const HostCoeffs& hc, unsigned* status,
+                                  cudaStream_t st);
+cudaError_t launch_step_d3q27_f16s(const void* fin, const void* gin, void* fout, void* gout,
+                                   const Geometry& geo, const HostCoeffs& hc, unsigned* status,
+                                   cudaStream_t st);
+
+cudaError_t launch_init(int dim, int prec, void* f, void* g, const Geometry& geo, double T_init,
+                        double T_ref, uint64_t seed, double perturb, cudaStream_t st);
+cudaError_t launch_fields(int dim, int prec, const void* f, const void* g, const Geometry& geo,
+                          const HostCoeffs& hc, double* rho, double* ux, double* uy, double* uz,
+                          double* T, cudaStream_t st);
+cudaError_t launch_get_pops(int dim, int prec, const void* f, const void* g, const Geometry& geo,
+                            double T_ref, double* fo, double* go, cudaStream_t st);
+cudaError_t launch_set_pops(int dim, int prec, void* f, void* g, const Geometry& geo, double T_ref,
+                            const double* fi, const double* gi, cudaStream_t st);
+
+// Local wall Nusselt numbers of a fixed-T face and their mean / max / min.
+// scratch must hold nusselt_scratch_doubles(n_face) doubles plus one unsigned ticket (ticket
+// must be zero on entry and is left zero on exit).  result receives
+// {sum, max, argmax, min, argmin} as doubles.
+size_t nusselt_scratch_doubles(long n_face);
+cudaError_t launch_nusselt(int dim, int prec, const void* f, const void* g, const Geometry& geo,
+                           const HostCoeffs& hc, int face, double scale, double* profile,
+                           double* scratch, unsigned* ticket, double* result, cudaStream_t st);
+
+}  // namespace lbm
+
+namespace lbm {
+
+template <class R, int QF, int QG>
+inline Coeffs<R, QF, QG> make_coeffs(const HostCoeffs& h)
+{
+    Coeffs<R, QF, QG> c{};
+    for (int a = 0; a < QF; ++a) {
+        c.om_f[a] = R(h.om_f[a]);
+        c.hf[a] = R(1.0 - 0.5 * h.om_f[a]);
+    }
+    for (int b = 0; b < QG; ++b) c.om_g[b] = R(h.om_g[b]);
+    c.gbeta = R(h.gbeta);
+    c.T_ref = R(h.T_ref);
+    c.gaxis = h.gaxis;
+    return c;
+}
+
+// Thread blocks of 256 threads, x-major so that a warp reads and writes 32 consecutive nodes.
+inline dim3 block_shape(int nx)
+{
+    const int bx = nx >= 128 ? 128 : ((nx + 31) / 32) * 32;
+    return dim3(bx, 256 / bx, 1);
+}
+
+inline dim3 grid_shape(const Geometry& g, dim3 b)
+{
+    return dim3((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y, g.nz);
+}
+
+}  // namespace lbm

@@ -1,0 +1,156 @@
+// lbm_common.cuh -- storage policies, geometry and the pull-with-walls link for the fused
+// collide-and-stream kernels of the Fokker-Planck central-moment LBM (arXiv 2504.09041).
+//
+// Layout in HBM: structure of arrays, one plane per link, f[a * n + i] with the node index
+// i = x + nx * (y + ny * z) (x fastest).  Two buffers per lattice (A -> B, then swap): the
+// kernels pull from the post-collision state of the previous step and write the new
+// post-collision state at the node itself, so every store is fully coalesced.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cstdint>
+#include <utility>
+#include <type_traits>
+
+namespace lbm {
+
+enum FaceKind { kPeriodic = 0, kAdiabatic = 1, kFixedT = 2 };
+
+// Storage policies: the type in HBM and the type of the moment algebra in registers.
+// FP16S stores the deviation from the rest populations (f_a - w_a, g_a - w_a T_o) so that the
+// 11-bit mantissa resolves the small departures from equilibrium.
+struct StoreF64 {
+    using T = double;
+    using R = double;
+    static constexpr bool kShift = false;
+    __device__ static R load(const T* p, size_t i, R) { return __ldg(p + i); }
+    __device__ static void store(T* p, size_t i, R v, R) { p[i] = v; }
+};
+struct StoreF32 {
+    using T = float;
+    using R = float;
+    static constexpr bool kShift = false;
+    __device__ static R load(const T* p, size_t i, R) { return __ldg(p + i); }
+    __device__ static void store(T* p, size_t i, R v, R) { p[i] = v; }
+};
+struct StoreF16S {
+    using T = __half;
+    using R = float;
+    static constexpr bool kShift = true;
+    __device__ static R load(const T* p, size_t i, R shift)
+    {
+        return shift + __half2float(__ldg(p + i));
+    }
+    __device__ static void store(T* p, size_t i, R v, R shift)
+    {
+        p[i] = __float2half_rn(v - shift);
+    }
+};
+
+// Box geometry and wall description shared by every kernel.
+struct Geometry {
+    int nx, ny, nz;
+    int nxy;                  // nx * ny
+    int n;                    // nx * ny * nz (< 2^31)
+    int kind[6];              // FaceKind of -x, +x, -y, +y, -z, +z
+    double T_wall[6];         // uniform wall temperature of fixed-T faces
+    const double* profile[6]; // per-node wall temperature (face tangential order) or nullptr
+};
+
+// Relaxation rates and coupling in the register type.
+template <class R, int QF, int QG>
+struct Coeffs {
+    R om_f[QF];   // omega of each relaxed flow moment
+    R hf[QF];     // 1 - omega/2 (source weight)
+    R om_g[QG];
+    R gbeta, T_ref;
+    int gaxis;    // 0, 1, 2
+};
+
+// Per-thread wall bookkeeping for the pull.  For an axis, "m" is a link whose source lies at
+// coordinate - 1 (component +1) and "p" one whose source lies at coordinate + 1 (component -1).
+template <class R>
+struct NodeWalls {
+    int wrap_m[3], wrap_p[3];   // linear-index correction when a periodic axis wraps
+    bool out_m[3], out_p[3];    // the source lies beyond a wall
+    bool fix_m[3], fix_p[3];    // ... and that wall has a fixed temperature
+    R tw_m[3], tw_p[3];         // wall temperature of that fixed-T face at this node
+};
+
+// Wall temperature of face f seen from node (x, y, z).
+__device__ __forceinline__ double wall_temperature(const Geometry& g, int f, int x, int y, int z)
+{
+    const double* p = g.profile[f];
+    if (p == nullptr) return g.T_wall[f];
+    const int ax = f >> 1;
+    const int t = ax == 0 ? y + g.ny * z : (ax == 1 ? x + g.nx * z : x + g.nx * y);
+    return __ldg(p + t);
+}
+
+template <class R>
+__device__ __forceinline__ NodeWalls<R> node_walls(const Geometry& g, int x, int y, int z, int dims)
+{
+    NodeWalls<R> w;
+    const int c[3] = {x, y, z};
+    const int ext[3] = {g.nx, g.ny, g.nz};
+    const int stride[3] = {1, g.nx, g.nxy};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const bool lo = c[ax] == 0, hi = c[ax] == ext[ax] - 1;
+        const bool per = ax >= dims || g.kind[2 * ax] == kPeriodic;
+        w.wrap_m[ax] = (lo && per) ? ext[ax] * stride[ax] : 0;
+        w.wrap_p[ax] = (hi && per) ? -ext[ax] * stride[ax] : 0;
+        w.out_m[ax] = lo && !per;
+        w.out_p[ax] = hi && !per;
+        w.fix_m[ax] = w.out_m[ax] && g.kind[2 * ax] == kFixedT;
+        w.fix_p[ax] = w.out_p[ax] && g.kind[2 * ax + 1] == kFixedT;
+        w.tw_m[ax] = w.fix_m[ax] ? R(wall_temperature(g, 2 * ax, x, y, z)) : R(0);
+        w.tw_p[ax] = w.fix_p[ax] ? R(wall_temperature(g, 2 * ax + 1, x, y, z)) : R(0);
+    }
+    return w;
+}
+
+// Source of the link arriving at node i along (EX, EY, EZ) after the walls.  Returns the
+// linear index of the source node.  *out is set when the source lies beyond a wall; *dir is
+// set when one of the crossed walls has a fixed temperature, and *tw is then the temperature of
+// the first such face in the order -x, +x, -y, +y, -z, +z.
+template <int EX, int EY, int EZ, class R>
+__device__ __forceinline__ int link_source(const Geometry& g, const NodeWalls<R>& w, int i,
+                                           bool* out, bool* dir, R* tw)
+{
+    int s = i - (EX + EY * g.nx + EZ * g.nxy);
+    bool o = false, d = false;
+    R t = R(0);
+    if (EX == 1) { s += w.wrap_m[0]; o |= w.out_m[0]; if (w.fix_m[0]) { d = true; t = w.tw_m[0]; } }
+    if (EX == -1) { s += w.wrap_p[0]; o |= w.out_p[0]; if (w.fix_p[0]) { d = true; t = w.tw_p[0]; } }
+    if (EY == 1) { s += w.wrap_m[1]; o |= w.out_m[1]; if (w.fix_m[1] && !d) { d = true; t = w.tw_m[1]; } }
+    if (EY == -1) { s += w.wrap_p[1]; o |= w.out_p[1]; if (w.fix_p[1] && !d) { d = true; t = w.tw_p[1]; } }
+    if (EZ == 1) { s += w.wrap_m[2]; o |= w.out_m[2]; if (w.fix_m[2] && !d) { d = true; t = w.tw_m[2]; } }
+    if (EZ == -1) { s += w.wrap_p[2]; o |= w.out_p[2]; if (w.fix_p[2] && !d) { d = true; t = w.tw_p[2]; } }
+    *out = o;
+    *dir = d;
+    *tw = t;
+    return s;
+}
+
+// Compile-time loop: calls f(std::integral_constant<int, 0>), ..., f(<N-1>).
+template <class F, int... Is>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, Is...>)
+{
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f)
+{
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// Divergence flag: bit 0 set when a node sees a non-finite or non-positive density or a
+// non-finite temperature.
+template <class R>
+__device__ __forceinline__ void check_node(unsigned* status, R rho, R T)
+{
+    if (!(rho > R(0)) || !(fabs(T) < R(1e30)) || !(rho < R(1e30))) atomicOr(status, 1u);
+}
+
+}  // namespace lbm

@@ -1,0 +1,32 @@
+// step2d.cu -- instantiations of the fused D2Q9 flow + D2Q9 energy step.
+#include "kernels.h"
+#include "step_d2q9.cuh"
+
+namespace lbm {
+
+template <class S>
+static cudaError_t run(const void* fin, const void* gin, void* fout, void* gout, const Geometry& geo,
+                       const HostCoeffs& hc, unsigned* status, cudaStream_t st)
+{
+    using T = typename S::T;
+    using R = typename S::R;
+    const dim3 b = block_shape(geo.nx);
+    const dim3 grid((geo.nx + b.x - 1) / b.x, (geo.ny + b.y - 1) / b.y, 1);
+    step_d2q9_kernel<S><<<grid, b, 0, st>>>((const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo,
+                                            make_coeffs<R, 9, 9>(hc), status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_d2q9(int prec, const void* fin, const void* gin, void* fout, void* gout,
+                             const Geometry& geo, const HostCoeffs& hc, unsigned* status,
+                             cudaStream_t st)
+{
+    switch (prec) {
+    case kF64: return run<StoreF64>(fin, gin, fout, gout, geo, hc, status, st);
+    case kF32: return run<StoreF32>(fin, gin, fout, gout, geo, hc, status, st);
+    case kF16S: return run<StoreF16S>(fin, gin, fout, gout, geo, hc, status, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lbm

@@ -1,0 +1,22 @@
+// step3d_f64.cu -- the fused D3Q27 flow + D3Q15 energy step with StoreF64 storage (one
+// translation unit per storage type so that the three heavy instantiations compile in parallel).
+#include "kernels.h"
+#include "step_d3q27.cuh"
+
+namespace lbm {
+
+cudaError_t launch_step_d3q27_f64(const void* fin, const void* gin, void* fout, void* gout,
+                                  const Geometry& geo, const HostCoeffs& hc, unsigned* status,
+                                  cudaStream_t st)
+{
+    using S = StoreF64;
+    using T = typename S::T;
+    using R = typename S::R;
+    const dim3 b = block_shape(geo.nx);
+    step_d3q27_kernel<S><<<grid_shape(geo, b), b, 0, st>>>((const T*)fin, (const T*)gin, (T*)fout,
+                                                           (T*)gout, geo, make_coeffs<R, 27, 15>(hc),
+                                                           status);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm
