@@ -61,7 +61,7 @@ def barrier(world: int):
 # Clocks during the timed region
 # ---------------------------------------------------------------------------------------------
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -71,6 +71,11 @@ class ClockSampler:
         self.gpu = ids[local_rank] if local_rank < len(ids) else str(local_rank)
         self.proc = None
         self.lines = []
+        self.window = None
+
+    def mark(self, start, end):
+        """Restrict the summary to samples taken between two datetime.now() marks."""
+        self.window = (start, end)
 
     def __enter__(self):
         try:
@@ -98,24 +103,29 @@ class ClockSampler:
             self.thread.join(timeout=2)
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        from datetime import datetime
+        sm, mx, reasons, power = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.lines:
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
+                ts = datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                if self.window and not (self.window[0] <= ts <= self.window[1]):
+                    continue
+                sm.append(float(parts[2]))
+                mx = float(parts[3])
+                power.append(float(parts[4]))
             except ValueError:
                 continue
-            for name, flag in zip(names, parts[5:9]):
+            for name, flag in zip(names, parts[6:10]):
                 if flag.lower() == "active":
                     reasons.add(name)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w_median": statistics.median(power) if power else None}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -178,15 +188,16 @@ def run_gpu(args):
     info = lat.info()
     bpn = info.bytes_per_node_update
 
-    # warm-up
-    lat.step(args.warmup)
-    lat.nusselt(0)
-    lat.sync()
-
+    from datetime import datetime
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    barrier(world)
-    torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
+        # warm-up (also gives the clock sampler time to start)
+        lat.step(args.warmup)
+        lat.nusselt(0)
+        lat.sync()
+        barrier(world)
+        torch.cuda.synchronize()
+        t_start = datetime.now()
         ev[0].record(stream)
         lat.step(args.steps)
         ev[1].record(stream)
@@ -194,6 +205,7 @@ def run_gpu(args):
         nu_cold = L.lbm_nusselt(lat.h, 1)
         ev[2].record(stream)
         torch.cuda.synchronize()
+        clocks.mark(t_start, datetime.now())
     barrier(world)
     lat.sync()
     t_total = ev[0].elapsed_time(ev[2]) / 1e3
@@ -266,7 +278,8 @@ def run_gpu(args):
                 "job": "set_state from pinned host + K steps + 2 wall Nusselt + T field to host"},
         "gpu_launches": launches,
         "clocks": clk,
-        "nusselt": {"hot_mean": nu_hot[0], "cold_mean": nu_cold[0], "steps_done": info.steps},
+        "nusselt": {"hot_mean": nu_hot[0], "cold_mean": nu_cold[0],
+                    "after_steps": args.warmup + args.steps},
     }
     if forms:
         line["per_form"] = forms
@@ -369,8 +382,8 @@ def run_reference(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

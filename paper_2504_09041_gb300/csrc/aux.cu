@@ -23,7 +23,8 @@ cudaError_t launch_step(int dim, int prec, const void* fin, const void* gin, voi
 }
 
 // ---------------------------------------------------------------------------------------------
-// Exact conversions between storage and double (FP16S: shift + deviation, formed in double).
+// Conversions between storage and double (F32 and F16S store deviations from the rest state;
+// the full value shift + deviation is formed in double).
 // ---------------------------------------------------------------------------------------------
 template <class S> struct Conv;
 template <> struct Conv<StoreF64> {
@@ -31,15 +32,18 @@ template <> struct Conv<StoreF64> {
     __device__ static void put(double* p, size_t i, double v, double) { p[i] = v; }
 };
 template <> struct Conv<StoreF32> {
-    __device__ static double get(const float* p, size_t i, double) { return (double)p[i]; }
-    __device__ static void put(float* p, size_t i, double v, double) { p[i] = (float)v; }
+    __device__ static double get(const float* p, size_t i, double s) { return s + (double)p[i]; }
+    __device__ static void put(float* p, size_t i, double v, double s) { p[i] = (float)(v - s); }
 };
 template <> struct Conv<StoreF16S> {
     __device__ static double get(const __half* p, size_t i, double s)
     {
-        return s + (double)__half2float(p[i]);
+        return s + (double)__half2float(p[i]) * (double)StoreF16S::kInvScale;
     }
-    __device__ static void put(__half* p, size_t i, double v, double s) { p[i] = __double2half(v - s); }
+    __device__ static void put(__half* p, size_t i, double v, double s)
+    {
+        p[i] = __double2half((v - s) * (double)StoreF16S::kScale);
+    }
 };
 
 template <int DIM> struct Lat;
@@ -109,7 +113,8 @@ __global__ void set_pops_kernel(typename S::T* f, typename S::T* g, Geometry geo
     }
 }
 
-// Streamed populations at one node (the pull of the step kernels, without the collision).
+// Streamed populations at one node as deviations from the rest state (the pull of the step
+// kernels, without the collision).
 template <class S, int DIM>
 __device__ __forceinline__ void pulled(const typename S::T* f, const typename S::T* g,
                                        const Geometry& geo, typename S::R T_ref, int x, int y, int z,
@@ -137,7 +142,7 @@ __global__ void fields_kernel(const typename S::T* f, const typename S::T* g, Ge
         const int x = (int)(i % geo.nx), y = (int)((i / geo.nx) % geo.ny), z = (int)(i / geo.nxy);
         R fo[L::QF], go[L::QG];
         pulled<S, DIM>(f, g, geo, R(hc.T_ref), x, y, z, fo, go);
-        double T = 0.0, r = 0.0, j[3] = {0.0, 0.0, 0.0};
+        double T = hc.T_ref, r = 1.0, j[3] = {0.0, 0.0, 0.0};
         for (int b = 0; b < L::QG; ++b) T += (double)go[b];
         for (int a = 0; a < L::QF; ++a) {
             r += (double)fo[a];
@@ -231,7 +236,7 @@ __global__ void __launch_bounds__(256)
             pulled<S, DIM>(f, g, geo, R(T_ref), c[0], c[1], c[2], fo, go);
             double s = 0.0;
             for (int b = 0; b < L::QG; ++b) s += (double)go[b];
-            Tl[l] = s;
+            Tl[l] = T_ref + s;
         }
         c[ax] = hi ? ext[ax] - 1 : 0;
         const double Tw = wall_temperature(geo, face, c[0], c[1], c[2]);

@@ -80,6 +80,12 @@ inline dim3 block_shape(int nx)
     return dim3(bx, 256 / bx, 1);
 }
 
+// 32-bit element offsets suffice when every population plane index q * n fits in 32 bits.
+inline bool index32(const Geometry& g, int q)
+{
+    return (unsigned long long)q * (unsigned long long)g.n <= 0xffffffffULL;
+}
+
 inline dim3 grid_shape(const Geometry& g, dim3 b)
 {
     return dim3((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y, g.nz);

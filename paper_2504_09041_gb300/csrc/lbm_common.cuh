@@ -16,35 +16,36 @@ namespace lbm {
 
 enum FaceKind { kPeriodic = 0, kAdiabatic = 1, kFixedT = 2 };
 
-// Storage policies: the type in HBM and the type of the moment algebra in registers.
-// FP16S stores the deviation from the rest populations (f_a - w_a, g_a - w_a T_o) so that the
-// 11-bit mantissa resolves the small departures from equilibrium.
+// Storage policies: the type in HBM and the type of the moment algebra in registers.  The
+// kernels work on deviations from the rest populations (f_a - w_a and g_a - w_a T_o), which keeps
+// every quantity of the collision small and resolves it to the register type's precision.
+//  - F64 stores the populations themselves and forms the deviation on load.
+//  - F32 stores the deviations.
+//  - F16S stores the deviations scaled by 2^10, so that deviations down to 6e-8 stay in FP16's
+//    normal range (full 11-bit significand) while |deviation| < 64 still fits; the scale is a
+//    power of two and adds no rounding.
 struct StoreF64 {
     using T = double;
     using R = double;
-    static constexpr bool kShift = false;
-    __device__ static R load(const T* p, size_t i, R) { return __ldg(p + i); }
-    __device__ static void store(T* p, size_t i, R v, R) { p[i] = v; }
+    __device__ static R load_dev(const T* p, size_t i, R shift) { return __ldg(p + i) - shift; }
+    __device__ static void store_dev(T* p, size_t i, R dev, R shift) { p[i] = shift + dev; }
 };
 struct StoreF32 {
     using T = float;
     using R = float;
-    static constexpr bool kShift = false;
-    __device__ static R load(const T* p, size_t i, R) { return __ldg(p + i); }
-    __device__ static void store(T* p, size_t i, R v, R) { p[i] = v; }
+    __device__ static R load_dev(const T* p, size_t i, R) { return __ldg(p + i); }
+    __device__ static void store_dev(T* p, size_t i, R dev, R) { p[i] = dev; }
 };
 struct StoreF16S {
     using T = __half;
     using R = float;
-    static constexpr bool kShift = true;
-    __device__ static R load(const T* p, size_t i, R shift)
+    static constexpr float kScale = 1024.0f;
+    static constexpr float kInvScale = 1.0f / 1024.0f;
+    __device__ static R load_dev(const T* p, size_t i, R)
     {
-        return shift + __half2float(__ldg(p + i));
+        return __half2float(__ldg(p + i)) * kInvScale;
     }
-    __device__ static void store(T* p, size_t i, R v, R shift)
-    {
-        p[i] = __float2half_rn(v - shift);
-    }
+    __device__ static void store_dev(T* p, size_t i, R dev, R) { p[i] = __float2half_rn(dev * kScale); }
 };
 
 // Box geometry and wall description shared by every kernel.

@@ -12,8 +12,13 @@ static cudaError_t run(const void* fin, const void* gin, void* fout, void* gout,
     using R = typename S::R;
     const dim3 b = block_shape(geo.nx);
     const dim3 grid((geo.nx + b.x - 1) / b.x, (geo.ny + b.y - 1) / b.y, 1);
-    step_d2q9_kernel<S><<<grid, b, 0, st>>>((const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo,
-                                            make_coeffs<R, 9, 9>(hc), status);
+    const auto c = make_coeffs<R, 9, 9>(hc);
+    if (index32(geo, 9))
+        step_d2q9_kernel<S, unsigned><<<grid, b, 0, st>>>((const T*)fin, (const T*)gin, (T*)fout,
+                                                          (T*)gout, geo, c, status);
+    else
+        step_d2q9_kernel<S, size_t><<<grid, b, 0, st>>>((const T*)fin, (const T*)gin, (T*)fout,
+                                                        (T*)gout, geo, c, status);
     return cudaGetLastError();
 }
 

@@ -13,9 +13,13 @@ cudaError_t launch_step_d3q27_f64(const void* fin, const void* gin, void* fout, 
     using T = typename S::T;
     using R = typename S::R;
     const dim3 b = block_shape(geo.nx);
-    step_d3q27_kernel<S><<<grid_shape(geo, b), b, 0, st>>>((const T*)fin, (const T*)gin, (T*)fout,
-                                                           (T*)gout, geo, make_coeffs<R, 27, 15>(hc),
-                                                           status);
+    const auto c = make_coeffs<R, 27, 15>(hc);
+    if (index32(geo, 27))
+        step_d3q27_kernel<S, unsigned><<<grid_shape(geo, b), b, 0, st>>>(
+            (const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo, c, status);
+    else
+        step_d3q27_kernel<S, size_t><<<grid_shape(geo, b), b, 0, st>>>(
+            (const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo, c, status);
     return cudaGetLastError();
 }
 

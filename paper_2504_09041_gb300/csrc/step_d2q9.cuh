@@ -3,6 +3,13 @@
 //
 // The raw -> central map of Steps 1-2 is done as two sweeps of 3-link lines (x, then y), which
 // equals P then F on the tensor-product D2Q9 set; Steps 4-5 are the inverse sweeps.
+//
+// Deviation form: the kernel carries delta_a = f_a - w_a and gamma_a = g_a - w_a T_o.  Because
+// the sweeps are linear, the central moments of f are those of the rest populations w at the
+// velocity u, K_ab = W_a(ux) W_b(uy) with W_0 = 1, W_1 = -u, W_2 = 1/3 + u^2, plus the central
+// moments D_ab of delta.  The relaxation is rewritten for the deviations D_ab -> T_ab
+// (kappa~_ab = K_ab + T_ab) with the O(1) parts of K cancelled analytically, so every quantity
+// in the collision is small and keeps the register type's full relative precision.
 #pragma once
 
 #include "lattices.cuh"
@@ -14,8 +21,10 @@ template <class R>
 using Coeffs2D = Coeffs<R, 9, 9>;
 
 // Streaming (Eqs. LBMsteps-stream, LBMsteps-streamg) with half-way bounce-back for f, and
-// bounce-back (adiabatic) or anti-bounce-back (fixed T) for g at the walls (Sec. 5.1).
-template <class S>
+// bounce-back (adiabatic) or anti-bounce-back (fixed T) for g at the walls (Sec. 5.1), in
+// deviations: the anti-bounce-back g_a = -g~_abar + 2 w_a T_w becomes
+// gamma_a = -gamma~_abar + 2 w_a (T_w - T_o).
+template <class S, class Idx = size_t>
 __device__ __forceinline__ void pull_d2q9(const typename S::T* __restrict__ fin,
                                           const typename S::T* __restrict__ gin, const Geometry& geo,
                                           const NodeWalls<typename S::R>& w, int i, typename S::R T_ref,
@@ -28,47 +37,57 @@ __device__ __forceinline__ void pull_d2q9(const typename S::T* __restrict__ fin,
         bool out, dir;
         R tw;
         const int s = link_source<e9(a, 0), e9(a, 1), 0>(geo, w, i, &out, &dir, &tw);
-        const size_t off = out ? (size_t)o * geo.n + i : (size_t)a * geo.n + s;
-        f[a] = S::load(fin, off, R(w9(a)));
-        const R gv = S::load(gin, off, R(w9(a)) * T_ref);
-        g[a] = dir ? R(2.0 * w9(a)) * tw - gv : gv;
+        const Idx off = out ? (Idx)o * geo.n + i : (Idx)a * geo.n + s;
+        f[a] = S::load_dev(fin, off, R(w9(a)));
+        const R gv = S::load_dev(gin, off, R(w9(a)) * T_ref);
+        g[a] = dir ? R(2.0 * w9(a)) * (tw - T_ref) - gv : gv;
     });
 }
 
-// Flow collision in central-moment space (App. A Step 3, readings R5 and R8 of the oracle's
-// notes: second-order sources vanish, sigma_12 carries the factor 2 of Eq. forcing:2D).
-// k[b][a] holds kappa_ab on entry and kappa~_ab on exit.
+// Flow collision (App. A Step 3; second-order sources vanish; sigma_12 carries the factor 2 of
+// Eq. forcing:2D) on the deviations: D[b][a] = kappa_ab - K_ab on entry, kappa~_ab - K_ab on exit.
 template <class R>
-__device__ __forceinline__ void relax_f_d2q9(R k[3][3], R rho, R irho, R Fx, R Fy, const Coeffs2D<R>& c)
+__device__ __forceinline__ void relax_f_d2q9(R D[3][3], R drho, R irho, R ux, R uy, R Fx, R Fy,
+                                             const Coeffs2D<R>& c)
 {
-    const R k00 = k[0][0], k10 = k[0][1], k20 = k[0][2];
-    const R k01 = k[1][0], k11 = k[1][1], k21 = k[1][2];
-    const R k02 = k[2][0], k12 = k[2][1], k22 = k[2][2];
+    const R third = R(1.0 / 3.0);
+    const R A = third + ux * ux, B = third + uy * uy;     // K_20, K_02
+    const R uxuy = ux * uy;                                // K_11
+    const R D00 = D[0][0], D10 = D[0][1], D20 = D[0][2];
+    const R D01 = D[1][0], D11 = D[1][1], D21 = D[1][2];
+    const R D02 = D[2][0], D12 = D[2][1], D22 = D[2][2];
     const R Fxr = Fx * irho, Fyr = Fy * irho;
+    // sources with the full pre-collision moments kappa = K + D
+    const R k11 = uxuy + D11, k20 = A + D20, k02 = B + D02;
+    const R k21 = D21 - A * uy, k12 = D12 - ux * B;
     const R s21 = R(2) * Fxr * k11 + Fyr * k20;
     const R s12 = Fxr * k02 + R(2) * Fyr * k11;
     const R s22 = R(2) * (Fxr * k12 + Fyr * k21);
 
-    const R t00 = k00 + c.om_f[0] * (rho - k00);
-    const R t10 = k10 - c.om_f[1] * k10 + c.hf[1] * Fx;
-    const R t01 = k01 - c.om_f[2] * k01 + c.hf[2] * Fy;
-    const R k2s = k20 + k02, k2d = k20 - k02;
-    const R t2s = k2s + c.om_f[3] * (R(2.0 / 3.0) * rho - k2s);
-    const R t2d = k2d - c.om_f[4] * k2d;
-    const R t11 = k11 - c.om_f[5] * k11;
-    const R t21 = k21 - c.om_f[6] * k21 + c.hf[6] * s21;
-    const R t12 = k12 - c.om_f[7] * k12 + c.hf[7] * s12;
-    const R t20 = R(0.5) * (t2s + t2d);
-    const R t02 = R(0.5) * (t2s - t2d);
-    const R Mv22 = (t20 * t02 + R(2) * t11 * t11) * irho;
-    const R t22 = k22 + c.om_f[8] * (Mv22 - k22) + c.hf[8] * s22;
+    const R T00 = D00 + c.om_f[0] * (drho - D00);
+    const R T10 = D10 - c.om_f[1] * (D10 - ux) + c.hf[1] * Fx;
+    const R T01 = D01 - c.om_f[2] * (D01 - uy) + c.hf[2] * Fy;
+    const R D2s = D20 + D02, D2d = D20 - D02;
+    const R u2s = ux * ux + uy * uy, u2d = ux * ux - uy * uy;
+    const R T2s = D2s + c.om_f[3] * (R(2.0 / 3.0) * drho - u2s - D2s);
+    const R T2d = D2d - c.om_f[4] * (D2d + u2d);
+    const R T11 = D11 - c.om_f[5] * (D11 + uxuy);
+    const R T21 = D21 - c.om_f[6] * (D21 - A * uy) + c.hf[6] * s21;
+    const R T12 = D12 - c.om_f[7] * (D12 - ux * B) + c.hf[7] * s12;
+    const R T20 = R(0.5) * (T2s + T2d);
+    const R T02 = R(0.5) * (T2s - T2d);
+    // kappa^Mv_22 - K_22 with t20 = A + T20, t02 = B + T02, t11 = uxuy + T11
+    const R t11 = uxuy + T11;
+    const R M22 = (A * T02 + B * T20 + T20 * T02 + R(2) * t11 * t11 - A * B * drho) * irho;
+    const R T22 = D22 + c.om_f[8] * (M22 - D22) + c.hf[8] * s22;
 
-    k[0][0] = t00; k[0][1] = t10; k[0][2] = t20;
-    k[1][0] = t01; k[1][1] = t11; k[1][2] = t21;
-    k[2][0] = t02; k[2][1] = t12; k[2][2] = t22;
+    D[0][0] = T00; D[0][1] = T10; D[0][2] = T20;
+    D[1][0] = T01; D[1][1] = T11; D[1][2] = T21;
+    D[2][0] = T02; D[2][1] = T12; D[2][2] = T22;
 }
 
-// Energy collision in central-moment space (App. B Step 3, option-A attractors Eq. MvT2D).
+// Energy collision in central-moment space on full values (App. B Step 3, option-A attractors
+// Eq. MvT2D); n[b][a] holds eta_ab on entry and eta~_ab on exit.
 template <class R>
 __device__ __forceinline__ void relax_g_d2q9(R n[3][3], R T, const Coeffs2D<R>& c)
 {
@@ -127,7 +146,7 @@ __device__ __forceinline__ void from_central_d2q9(R p[3][3], R f[9], R ux, R uy)
 
 // One time step at one node: pull, macroscopic fields (App. A Step 7, App. B Step 7, Sec. 5.1
 // Boussinesq force), collide f and g, store.
-template <class S>
+template <class S, class Idx>
 __device__ __forceinline__ void node_step_d2q9(const typename S::T* __restrict__ fin,
                                                const typename S::T* __restrict__ gin,
                                                typename S::T* __restrict__ fout,
@@ -139,15 +158,18 @@ __device__ __forceinline__ void node_step_d2q9(const typename S::T* __restrict__
     const int i = x + geo.nx * y;
     const NodeWalls<R> w = node_walls<R>(geo, x, y, 0, 2);
     R f[9], g[9];
-    pull_d2q9<S>(fin, gin, geo, w, i, c.T_ref, f, g);
+    pull_d2q9<S, Idx>(fin, gin, geo, w, i, c.T_ref, f, g);
 
-    const R T = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-    const R rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    // rho = 1 + sum delta, rho u = sum delta e + F/2, T = T_o + sum gamma (sum w = 1, sum w e = 0)
+    const R dT = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    const R drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     const R jx = (f[1] + f[5] + f[8]) - (f[3] + f[6] + f[7]);
     const R jy = (f[2] + f[5] + f[6]) - (f[4] + f[7] + f[8]);
-    const R Fb = c.gbeta * (T - c.T_ref);
+    const R Fb = c.gbeta * dT;
     const R Fx = c.gaxis == 0 ? Fb : R(0);
     const R Fy = c.gaxis == 1 ? Fb : R(0);
+    const R rho = R(1) + drho;
+    const R T = c.T_ref + dT;
     const R irho = R(1) / rho;
     const R ux = (jx + R(0.5) * Fx) * irho;
     const R uy = (jy + R(0.5) * Fy) * irho;
@@ -155,21 +177,26 @@ __device__ __forceinline__ void node_step_d2q9(const typename S::T* __restrict__
 
     R p[3][3];
     to_central_d2q9(f, p, ux, uy);
-    relax_f_d2q9(p, rho, irho, Fx, Fy, c);
+    relax_f_d2q9(p, drho, irho, ux, uy, Fx, Fy, c);
     from_central_d2q9(p, f, ux, uy);
 
+    // energy populations on full values: g = w T_o + gamma
+    static_for<9>([&](auto A) {
+        constexpr int a = decltype(A)::value;
+        g[a] += R(w9(a)) * c.T_ref;
+    });
     to_central_d2q9(g, p, ux, uy);
     relax_g_d2q9(p, T, c);
     from_central_d2q9(p, g, ux, uy);
 
     static_for<9>([&](auto A) {
         constexpr int a = decltype(A)::value;
-        S::store(fout, (size_t)a * geo.n + i, f[a], R(w9(a)));
-        S::store(gout, (size_t)a * geo.n + i, g[a], R(w9(a)) * c.T_ref);
+        S::store_dev(fout, (Idx)a * geo.n + i, f[a], R(w9(a)));
+        S::store_dev(gout, (Idx)a * geo.n + i, g[a] - R(w9(a)) * c.T_ref, R(w9(a)) * c.T_ref);
     });
 }
 
-template <class S>
+template <class S, class Idx>
 __global__ void __launch_bounds__(256)
     step_d2q9_kernel(const typename S::T* __restrict__ fin, const typename S::T* __restrict__ gin,
                      typename S::T* __restrict__ fout, typename S::T* __restrict__ gout, Geometry geo,
@@ -178,7 +205,7 @@ __global__ void __launch_bounds__(256)
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= geo.nx || y >= geo.ny) return;
-    node_step_d2q9<S>(fin, gin, fout, gout, geo, c, status, x, y);
+    node_step_d2q9<S, Idx>(fin, gin, fout, gout, geo, c, status, x, y);
 }
 
 }  // namespace lbm

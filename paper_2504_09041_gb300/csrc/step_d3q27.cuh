@@ -6,6 +6,13 @@
 // D3Q15: raw moments come from the six axis links in pairs and from an 8-point Walsh-Hadamard
 // transform of the corner links (the structure of App. C Step 1); the central shift and its exact
 // inverse are applied axis by axis (Steps 2 and 4, including the aliased moment 220).
+//
+// Deviation form: the kernel carries delta_a = f_a - w_a and gamma_b = g_b - w_b T_o.  The central
+// moments of f are those of the rest populations at the velocity u, K_abc = W_a(ux) W_b(uy)
+// W_c(uz) with W_0 = 1, W_1 = -u, W_2 = 1/3 + u^2, plus the central moments D_abc of delta; the
+// flow relaxation is written for the deviations with the O(1) parts of K (the moments even in
+// every direction) cancelled analytically, so the FP32 arithmetic resolves the small departures
+// from rest.
 #pragma once
 
 #include "lattices.cuh"
@@ -22,7 +29,7 @@ __host__ __device__ constexpr int g15_of_27(int a)
     return a < 7 ? a : (a >= 19 ? a - 12 : -1);
 }
 
-template <class S>
+template <class S, class Idx = size_t>
 __device__ __forceinline__ void pull_d3q27_d3q15(const typename S::T* __restrict__ fin,
                                                  const typename S::T* __restrict__ gin,
                                                  const Geometry& geo,
@@ -37,108 +44,134 @@ __device__ __forceinline__ void pull_d3q27_d3q15(const typename S::T* __restrict
         bool out, dir;
         R tw;
         const int s = link_source<e27(a, 0), e27(a, 1), e27(a, 2)>(geo, w, i, &out, &dir, &tw);
-        const size_t off = out ? (size_t)o * geo.n + i : (size_t)a * geo.n + s;
-        f[a] = S::load(fin, off, R(w27(a)));
+        const Idx off = out ? (Idx)o * geo.n + i : (Idx)a * geo.n + s;
+        f[a] = S::load_dev(fin, off, R(w27(a)));
         constexpr int b = g15_of_27(a);
         if constexpr (b >= 0) {
             constexpr int ob = opp15(b);
-            const size_t og = out ? (size_t)ob * geo.n + i : (size_t)b * geo.n + s;
-            const R gv = S::load(gin, og, R(w15(b)) * T_ref);
-            g[b] = dir ? R(2.0 * w15(b)) * tw - gv : gv;
+            const Idx og = out ? (Idx)ob * geo.n + i : (Idx)b * geo.n + s;
+            const R gv = S::load_dev(gin, og, R(w15(b)) * T_ref);
+            g[b] = dir ? R(2.0 * w15(b)) * (tw - T_ref) - gv : gv;
         }
     });
 }
 
-// Flow collision in central-moment space, K[c][b][a] = kappa_abc (reading R6 of the oracle notes).
-// Rate slots follow the moment order of Sec. 4.2; slot 7 is the trace (bulk), slots 8 and 9 the
-// deviators kappa_200 - kappa_020 and kappa_200 - kappa_002.
+// Flow collision (reading R6 of the oracle notes) on the deviations: D[c][b][a] = kappa_abc - K_abc
+// on entry, kappa~_abc - K_abc on exit.  Rate slots follow the moment order of Sec. 4.2; slot 7
+// relaxes the trace (bulk), slots 8 and 9 the deviators kappa_200 - kappa_020, kappa_200 - kappa_002.
+// Sources (Eq. forcing:3D) use the full pre-collision moments kappa = K + D.
 template <class R>
-__device__ __forceinline__ void relax_f_d3q27(R K[3][3][3], R rho, R irho, R Fx, R Fy, R Fz,
-                                              const Coeffs3D<R>& c)
+__device__ __forceinline__ void relax_f_d3q27(R D[3][3][3], R drho, R irho, R ux, R uy, R uz, R Fx,
+                                              R Fy, R Fz, const Coeffs3D<R>& c)
 {
-#define KK(a, b, cc) K[cc][b][a]
-    const R Fxr = Fx * irho, Fyr = Fy * irho, Fzr = Fz * irho;
+#define DD(a, b, cc) D[cc][b][a]
     const R* om = c.om_f;
     const R* h = c.hf;
-
-    // orders 0 and 1
-    const R t000 = KK(0, 0, 0) + om[0] * (rho - KK(0, 0, 0));
-    const R t100 = KK(1, 0, 0) - om[1] * KK(1, 0, 0) + h[1] * Fx;
-    const R t010 = KK(0, 1, 0) - om[2] * KK(0, 1, 0) + h[2] * Fy;
-    const R t001 = KK(0, 0, 1) - om[3] * KK(0, 0, 1) + h[3] * Fz;
-
-    // order 2
-    const R k200 = KK(2, 0, 0), k020 = KK(0, 2, 0), k002 = KK(0, 0, 2);
-    const R k110 = KK(1, 1, 0), k101 = KK(1, 0, 1), k011 = KK(0, 1, 1);
-    const R t110 = k110 - om[4] * k110;
-    const R t101 = k101 - om[5] * k101;
-    const R t011 = k011 - om[6] * k011;
-    const R tr = k200 + k020 + k002;
-    const R d1 = k200 - k020, d2 = k200 - k002;
-    const R trt = tr + om[7] * (rho - tr);       // 3 c_s^2 rho = rho
-    const R d1t = d1 - om[8] * d1;
-    const R d2t = d2 - om[9] * d2;
     const R third = R(1.0 / 3.0);
-    const R t200 = third * (trt + d1t + d2t);
-    const R t020 = third * (trt - R(2) * d1t + d2t);
-    const R t002 = third * (trt + d1t - R(2) * d2t);
+    const R Fxr = Fx * irho, Fyr = Fy * irho, Fzr = Fz * irho;
+    // rest moments at u: W_2 per axis, products of W_1
+    const R A = third + ux * ux, B = third + uy * uy, C = third + uz * uz;
+    const R xy = ux * uy, xz = ux * uz, yz = uy * uz;
 
-    // order 3: attractors zero, sources from the pre-collision moments
-    const R k120 = KK(1, 2, 0), k102 = KK(1, 0, 2), k210 = KK(2, 1, 0);
-    const R k012 = KK(0, 1, 2), k201 = KK(2, 0, 1), k021 = KK(0, 2, 1), k111 = KK(1, 1, 1);
-    const R t120 = k120 - om[10] * k120 + h[10] * (Fxr * k020 + R(2) * Fyr * k110);
-    const R t102 = k102 - om[11] * k102 + h[11] * (Fxr * k002 + R(2) * Fzr * k101);
-    const R t210 = k210 - om[12] * k210 + h[12] * (R(2) * Fxr * k110 + Fyr * k200);
-    const R t012 = k012 - om[13] * k012 + h[13] * (Fyr * k002 + R(2) * Fzr * k011);
-    const R t201 = k201 - om[14] * k201 + h[14] * (R(2) * Fxr * k101 + Fzr * k200);
-    const R t021 = k021 - om[15] * k021 + h[15] * (R(2) * Fyr * k011 + Fzr * k020);
-    const R t111 = k111 - om[16] * k111 + h[16] * (Fxr * k011 + Fyr * k101 + Fzr * k110);
+    // pre-collision deviations
+    const R d000 = DD(0, 0, 0), d100 = DD(1, 0, 0), d010 = DD(0, 1, 0), d001 = DD(0, 0, 1);
+    const R d110 = DD(1, 1, 0), d101 = DD(1, 0, 1), d011 = DD(0, 1, 1);
+    const R d200 = DD(2, 0, 0), d020 = DD(0, 2, 0), d002 = DD(0, 0, 2);
+    const R d120 = DD(1, 2, 0), d102 = DD(1, 0, 2), d210 = DD(2, 1, 0), d012 = DD(0, 1, 2);
+    const R d201 = DD(2, 0, 1), d021 = DD(0, 2, 1), d111 = DD(1, 1, 1);
+    const R d220 = DD(2, 2, 0), d202 = DD(2, 0, 2), d022 = DD(0, 2, 2);
+    const R d211 = DD(2, 1, 1), d121 = DD(1, 2, 1), d112 = DD(1, 1, 2);
+    const R d122 = DD(1, 2, 2), d212 = DD(2, 1, 2), d221 = DD(2, 2, 1), d222 = DD(2, 2, 2);
 
-    // order 4: attractors from post-collision order 2
-    const R k220 = KK(2, 2, 0), k202 = KK(2, 0, 2), k022 = KK(0, 2, 2);
-    const R k211 = KK(2, 1, 1), k121 = KK(1, 2, 1), k112 = KK(1, 1, 2);
-    const R M220 = (t200 * t020 + R(2) * t110 * t110) * irho;
-    const R M202 = (t200 * t002 + R(2) * t101 * t101) * irho;
-    const R M022 = (t020 * t002 + R(2) * t011 * t011) * irho;
-    const R M211 = (t200 * t011 + R(2) * t110 * t101) * irho;
-    const R M121 = (t020 * t101 + R(2) * t110 * t011) * irho;
-    const R M112 = (t002 * t110 + R(2) * t011 * t101) * irho;
-    const R t220 = k220 + om[17] * (M220 - k220) + h[17] * R(2) * (Fxr * k120 + Fyr * k210);
-    const R t202 = k202 + om[18] * (M202 - k202) + h[18] * R(2) * (Fxr * k102 + Fzr * k201);
-    const R t022 = k022 + om[19] * (M022 - k022) + h[19] * R(2) * (Fyr * k012 + Fzr * k021);
-    const R t211 = k211 + om[20] * (M211 - k211) + h[20] * (R(2) * Fxr * k111 + Fyr * k201 + Fzr * k210);
-    const R t121 = k121 + om[21] * (M121 - k121) + h[21] * (Fxr * k021 + R(2) * Fyr * k111 + Fzr * k120);
-    const R t112 = k112 + om[22] * (M112 - k112) + h[22] * (Fxr * k012 + Fyr * k102 + R(2) * Fzr * k111);
+    // full pre-collision moments needed by the sources
+    const R k110 = xy + d110, k101 = xz + d101, k011 = yz + d011;
+    const R k200 = A + d200, k020 = B + d020, k002 = C + d002;
+    const R k120 = d120 - ux * B, k102 = d102 - ux * C, k210 = d210 - A * uy;
+    const R k012 = d012 - uy * C, k201 = d201 - A * uz, k021 = d021 - B * uz;
+    const R k111 = d111 - xy * uz;
+    const R k220 = A * B + d220;
+    const R k211 = A * yz + d211, k121 = B * xz + d121, k112 = C * xy + d112;
+    const R k022 = B * C + d022, k202 = A * C + d202;
+    const R k122 = d122 - ux * B * C, k212 = d212 - A * uy * C, k221 = d221 - A * B * uz;
 
-    // order 5: attractors from post-collision orders 2 and 3
-    const R k122 = KK(1, 2, 2), k212 = KK(2, 1, 2), k221 = KK(2, 2, 1);
-    const R two5 = R(2.0 / 5.0) * irho;
-    const R M122 = two5 * (t020 * t102 + t002 * t120 + R(4) * t011 * t111
-                           + R(2) * (t101 * t021 + t110 * t012));
-    const R M212 = two5 * (t200 * t012 + t002 * t210 + R(4) * t101 * t111
-                           + R(2) * (t110 * t102 + t011 * t201));
-    const R M221 = two5 * (t200 * t021 + t020 * t201 + R(4) * t110 * t111
-                           + R(2) * (t011 * t210 + t101 * t120));
-    const R t122 = k122 + om[23] * (M122 - k122) + h[23] * (Fxr * k022 + R(2) * (Fyr * k112 + Fzr * k121));
-    const R t212 = k212 + om[24] * (M212 - k212) + h[24] * (Fyr * k202 + R(2) * (Fxr * k112 + Fzr * k211));
-    const R t221 = k221 + om[25] * (M221 - k221) + h[25] * (Fzr * k220 + R(2) * (Fxr * k121 + Fyr * k211));
+    // orders 0 and 1 (K_000 = 1, K_100 = -ux, ...)
+    const R t000 = d000 + om[0] * (drho - d000);
+    const R t100 = d100 - om[1] * (d100 - ux) + h[1] * Fx;
+    const R t010 = d010 - om[2] * (d010 - uy) + h[2] * Fy;
+    const R t001 = d001 - om[3] * (d001 - uz) + h[3] * Fz;
 
-    // order 6: attractor from post-collision orders 2 and 4
-    const R k222 = KK(2, 2, 2);
+    // order 2: off-diagonal toward 0, trace toward rho, deviators toward 0
+    const R t110 = d110 - om[4] * (d110 + xy);
+    const R t101 = d101 - om[5] * (d101 + xz);
+    const R t011 = d011 - om[6] * (d011 + yz);
+    const R dtr = d200 + d020 + d002;
+    const R dd1 = d200 - d020, dd2 = d200 - d002;
+    const R ttr = dtr + om[7] * (drho - (ux * ux + uy * uy + uz * uz) - dtr);
+    const R td1 = dd1 - om[8] * (dd1 + ux * ux - uy * uy);
+    const R td2 = dd2 - om[9] * (dd2 + ux * ux - uz * uz);
+    const R t200 = third * (ttr + td1 + td2);
+    const R t020 = third * (ttr - R(2) * td1 + td2);
+    const R t002 = third * (ttr + td1 - R(2) * td2);
+
+    // order 3: attractors zero
+    const R t120 = d120 - om[10] * k120 + h[10] * (Fxr * k020 + R(2) * Fyr * k110);
+    const R t102 = d102 - om[11] * k102 + h[11] * (Fxr * k002 + R(2) * Fzr * k101);
+    const R t210 = d210 - om[12] * k210 + h[12] * (R(2) * Fxr * k110 + Fyr * k200);
+    const R t012 = d012 - om[13] * k012 + h[13] * (Fyr * k002 + R(2) * Fzr * k011);
+    const R t201 = d201 - om[14] * k201 + h[14] * (R(2) * Fxr * k101 + Fzr * k200);
+    const R t021 = d021 - om[15] * k021 + h[15] * (R(2) * Fyr * k011 + Fzr * k020);
+    const R t111 = d111 - om[16] * k111 + h[16] * (Fxr * k011 + Fyr * k101 + Fzr * k110);
+
+    // full post-collision moments of orders 2-3 (small, or O(1) only through A, B, C)
+    const R p110 = xy + t110, p101 = xz + t101, p011 = yz + t011;
+    const R p120 = t120 - ux * B, p102 = t102 - ux * C, p210 = t210 - A * uy;
+    const R p012 = t012 - uy * C, p201 = t201 - A * uz, p021 = t021 - B * uz;
+    const R p111 = t111 - xy * uz;
+
+    // order 4: attractor minus K, with the O(1) products cancelled
+    const R M220 = (A * t020 + B * t200 + t200 * t020 + R(2) * p110 * p110 - A * B * drho) * irho;
+    const R M202 = (A * t002 + C * t200 + t200 * t002 + R(2) * p101 * p101 - A * C * drho) * irho;
+    const R M022 = (B * t002 + C * t020 + t020 * t002 + R(2) * p011 * p011 - B * C * drho) * irho;
+    const R M211 = ((A + t200) * p011 + R(2) * p110 * p101) * irho - A * yz;
+    const R M121 = ((B + t020) * p101 + R(2) * p110 * p011) * irho - B * xz;
+    const R M112 = ((C + t002) * p110 + R(2) * p011 * p101) * irho - C * xy;
+    const R t220 = d220 + om[17] * (M220 - d220) + h[17] * R(2) * (Fxr * k120 + Fyr * k210);
+    const R t202 = d202 + om[18] * (M202 - d202) + h[18] * R(2) * (Fxr * k102 + Fzr * k201);
+    const R t022 = d022 + om[19] * (M022 - d022) + h[19] * R(2) * (Fyr * k012 + Fzr * k021);
+    const R t211 = d211 + om[20] * (M211 - d211) + h[20] * (R(2) * Fxr * k111 + Fyr * k201 + Fzr * k210);
+    const R t121 = d121 + om[21] * (M121 - d121) + h[21] * (Fxr * k021 + R(2) * Fyr * k111 + Fzr * k120);
+    const R t112 = d112 + om[22] * (M112 - d112) + h[22] * (Fxr * k012 + Fyr * k102 + R(2) * Fzr * k111);
+
+    // order 5: attractors from post-collision orders 2 and 3 (K_122 = -ux B C, ...)
+    const R f25 = R(2.0 / 5.0) * irho;
+    const R q200 = A + t200, q020 = B + t020, q002 = C + t002;
+    const R M122 = f25 * (q020 * p102 + q002 * p120 + R(4) * p011 * p111
+                          + R(2) * (p101 * p021 + p110 * p012)) + ux * B * C;
+    const R M212 = f25 * (q200 * p012 + q002 * p210 + R(4) * p101 * p111
+                          + R(2) * (p110 * p102 + p011 * p201)) + A * uy * C;
+    const R M221 = f25 * (q200 * p021 + q020 * p201 + R(4) * p110 * p111
+                          + R(2) * (p011 * p210 + p101 * p120)) + A * B * uz;
+    const R t122 = d122 + om[23] * (M122 - d122) + h[23] * (Fxr * k022 + R(2) * (Fyr * k112 + Fzr * k121));
+    const R t212 = d212 + om[24] * (M212 - d212) + h[24] * (Fyr * k202 + R(2) * (Fxr * k112 + Fzr * k211));
+    const R t221 = d221 + om[25] * (M221 - d221) + h[25] * (Fzr * k220 + R(2) * (Fxr * k121 + Fyr * k211));
+
+    // order 6: attractor from post-collision orders 2 and 4, K_222 = A B C
+    const R p112 = C * xy + t112, p121 = B * xz + t121, p211 = A * yz + t211;
     const R M222 = third * irho
-                 * (t200 * t022 + t020 * t202 + t002 * t220
-                    + R(4) * (t110 * t112 + t101 * t121 + t011 * t211));
-    const R t222 = k222 + om[26] * (M222 - k222) + h[26] * R(2) * (Fxr * k122 + Fyr * k212 + Fzr * k221);
+                 * (A * t022 + B * t202 + C * t220 + B * C * t200 + A * C * t020 + A * B * t002
+                    + t200 * t022 + t020 * t202 + t002 * t220
+                    + R(4) * (p110 * p112 + p101 * p121 + p011 * p211) - R(3) * A * B * C * drho);
+    const R t222 = d222 + om[26] * (M222 - d222) + h[26] * R(2) * (Fxr * k122 + Fyr * k212 + Fzr * k221);
 
-    KK(0, 0, 0) = t000; KK(1, 0, 0) = t100; KK(0, 1, 0) = t010; KK(0, 0, 1) = t001;
-    KK(1, 1, 0) = t110; KK(1, 0, 1) = t101; KK(0, 1, 1) = t011;
-    KK(2, 0, 0) = t200; KK(0, 2, 0) = t020; KK(0, 0, 2) = t002;
-    KK(1, 2, 0) = t120; KK(1, 0, 2) = t102; KK(2, 1, 0) = t210; KK(0, 1, 2) = t012;
-    KK(2, 0, 1) = t201; KK(0, 2, 1) = t021; KK(1, 1, 1) = t111;
-    KK(2, 2, 0) = t220; KK(2, 0, 2) = t202; KK(0, 2, 2) = t022;
-    KK(2, 1, 1) = t211; KK(1, 2, 1) = t121; KK(1, 1, 2) = t112;
-    KK(1, 2, 2) = t122; KK(2, 1, 2) = t212; KK(2, 2, 1) = t221; KK(2, 2, 2) = t222;
-#undef KK
+    DD(0, 0, 0) = t000; DD(1, 0, 0) = t100; DD(0, 1, 0) = t010; DD(0, 0, 1) = t001;
+    DD(1, 1, 0) = t110; DD(1, 0, 1) = t101; DD(0, 1, 1) = t011;
+    DD(2, 0, 0) = t200; DD(0, 2, 0) = t020; DD(0, 0, 2) = t002;
+    DD(1, 2, 0) = t120; DD(1, 0, 2) = t102; DD(2, 1, 0) = t210; DD(0, 1, 2) = t012;
+    DD(2, 0, 1) = t201; DD(0, 2, 1) = t021; DD(1, 1, 1) = t111;
+    DD(2, 2, 0) = t220; DD(2, 0, 2) = t202; DD(0, 2, 2) = t022;
+    DD(2, 1, 1) = t211; DD(1, 2, 1) = t121; DD(1, 1, 2) = t112;
+    DD(1, 2, 2) = t122; DD(2, 1, 2) = t212; DD(2, 2, 1) = t221; DD(2, 2, 2) = t222;
+#undef DD
 }
 
 template <class R>
@@ -300,7 +333,7 @@ __device__ __forceinline__ void collide_g_d3q15(R g[15], R T, R ux, R uy, R uz, 
     g[14] = e * (D0 - D1_);
 }
 
-template <class S>
+template <class S, class Idx>
 __device__ __forceinline__ void node_step_d3q27(const typename S::T* __restrict__ fin,
                                                 const typename S::T* __restrict__ gin,
                                                 typename S::T* __restrict__ fout,
@@ -312,15 +345,16 @@ __device__ __forceinline__ void node_step_d3q27(const typename S::T* __restrict_
     const int i = x + geo.nx * y + geo.nxy * z;
     const NodeWalls<R> w = node_walls<R>(geo, x, y, z, 3);
     R f[27], g[15];
-    pull_d3q27_d3q15<S>(fin, gin, geo, w, i, c.T_ref, f, g);
+    pull_d3q27_d3q15<S, Idx>(fin, gin, geo, w, i, c.T_ref, f, g);
 
-    R T = g[0];
+    // rho = 1 + sum delta, rho u = sum delta e + F/2, T = T_o + sum gamma
+    R dT = g[0];
 #pragma unroll
-    for (int b = 1; b < 15; ++b) T += g[b];
-    R rho = f[0], jx = R(0), jy = R(0), jz = R(0);
+    for (int b = 1; b < 15; ++b) dT += g[b];
+    R drho = f[0], jx = R(0), jy = R(0), jz = R(0);
     static_for<26>([&](auto A) {
         constexpr int a = decltype(A)::value + 1;
-        rho += f[a];
+        drho += f[a];
         if (e27(a, 0) == 1) jx += f[a];
         if (e27(a, 0) == -1) jx -= f[a];
         if (e27(a, 1) == 1) jy += f[a];
@@ -328,10 +362,12 @@ __device__ __forceinline__ void node_step_d3q27(const typename S::T* __restrict_
         if (e27(a, 2) == 1) jz += f[a];
         if (e27(a, 2) == -1) jz -= f[a];
     });
-    const R Fb = c.gbeta * (T - c.T_ref);
+    const R Fb = c.gbeta * dT;
     const R Fx = c.gaxis == 0 ? Fb : R(0);
     const R Fy = c.gaxis == 1 ? Fb : R(0);
     const R Fz = c.gaxis == 2 ? Fb : R(0);
+    const R rho = R(1) + drho;
+    const R T = c.T_ref + dT;
     const R irho = R(1) / rho;
     const R ux = (jx + R(0.5) * Fx) * irho;
     const R uy = (jy + R(0.5) * Fy) * irho;
@@ -341,18 +377,23 @@ __device__ __forceinline__ void node_step_d3q27(const typename S::T* __restrict_
     {
         R p[3][3][3];
         to_central_d3q27(f, p, ux, uy, uz);
-        relax_f_d3q27(p, rho, irho, Fx, Fy, Fz, c);
+        relax_f_d3q27(p, drho, irho, ux, uy, uz, Fx, Fy, Fz, c);
         from_central_d3q27(p, f, ux, uy, uz);
     }
+    // energy populations on full values: g = w T_o + gamma
+    static_for<15>([&](auto B) {
+        constexpr int b = decltype(B)::value;
+        g[b] += R(w15(b)) * c.T_ref;
+    });
     collide_g_d3q15(g, T, ux, uy, uz, c.om_g);
 
     static_for<27>([&](auto A) {
         constexpr int a = decltype(A)::value;
-        S::store(fout, (size_t)a * geo.n + i, f[a], R(w27(a)));
+        S::store_dev(fout, (Idx)a * geo.n + i, f[a], R(w27(a)));
     });
-    static_for<15>([&](auto A) {
-        constexpr int b = decltype(A)::value;
-        S::store(gout, (size_t)b * geo.n + i, g[b], R(w15(b)) * c.T_ref);
+    static_for<15>([&](auto B) {
+        constexpr int b = decltype(B)::value;
+        S::store_dev(gout, (Idx)b * geo.n + i, g[b] - R(w15(b)) * c.T_ref, R(w15(b)) * c.T_ref);
     });
 }
 
@@ -361,7 +402,7 @@ struct Launch3D {
     static constexpr int kMinBlocks = sizeof(typename S::R) == 8 ? 1 : 2;
 };
 
-template <class S>
+template <class S, class Idx>
 __global__ void __launch_bounds__(256, Launch3D<S>::kMinBlocks)
     step_d3q27_kernel(const typename S::T* __restrict__ fin, const typename S::T* __restrict__ gin,
                       typename S::T* __restrict__ fout, typename S::T* __restrict__ gout,
@@ -371,7 +412,7 @@ __global__ void __launch_bounds__(256, Launch3D<S>::kMinBlocks)
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= geo.nx || y >= geo.ny) return;
-    node_step_d3q27<S>(fin, gin, fout, gout, geo, c, status, x, y, z);
+    node_step_d3q27<S, Idx>(fin, gin, fout, gout, geo, c, status, x, y, z);
 }
 
 }  // namespace lbm
