@@ -187,6 +187,41 @@ LBM_API int lbm_set_state(lbm_handle h, const void* buf, size_t bytes);
 LBM_API const char* lbm_last_error(lbm_handle h);
 LBM_API const char* lbm_status_string(int status);
 
+/*
+ * Wall Nusselt reduction that allocates nothing.  The paper has no counterpart: this is the
+ * lbm_nusselt computation offered to callers that may not allocate device memory.  Such callers
+ * own all of their device memory through another allocator (a framework's caching pool, or a
+ * fixed budget reserved at start-up); a cudaMalloc issued behind their back by a library would
+ * fail or break their accounting.  This call needs no handle and calls no cudaMalloc, cudaFree or
+ * other allocating routine.  The caller passes the energy populations and a result buffer it
+ * owns; the only other memory, one partial result per 256 wall nodes and a counter, is a fixed
+ * array inside the library (about 160 KB, held on every GPU that loads the library until the
+ * process exits).
+ *
+ *  lattice    lbm_lattice OR-ed with the lbm_prec of the population buffer.
+ *  nx..nz     box size (nz = 1 in 2D); face_kind, T_wall and T_ref as in lbm_bc.
+ *  g          device pointer to the energy populations [q_g][nz][ny][nx] in that precision's
+ *             storage format: LBM_FP64 holds g itself (the layout lbm_get_populations writes),
+ *             LBM_FP32 holds g - w T_ref as float, LBM_FP16S holds (g - w T_ref) * 2^10 as half
+ *             (the layouts lbm_get_state writes after its 64-byte header).
+ *  face       a fixed-temperature face; L and dT as in lbm_info_t.
+ *  result     device pointer to 5 doubles: mean Nu, max Nu, its tangential node index, min Nu,
+ *             its index (indices stored as doubles), with the definitions of lbm_nusselt.
+ *  stream     cudaStream_t to run on (NULL = legacy stream); the call returns without waiting.
+ * Errors: LBM_EINVAL for a bad argument, including a face with more than
+ * LBM_NUSSELT_STATIC_MAX_FACE_NODES nodes (the scratch array has room for that many);
+ * LBM_ECUDA if a CUDA call fails.
+ * The first call on each device performs a one-time set-up with that device current: it looks
+ * up the device address of the scratch array.  Make that first call before any stream capture
+ * begins.  Every call uses the same scratch array, which keeps the last call's contents: calls
+ * that may run at the same time on the GPU (on unordered streams, or from several host threads)
+ * race and give wrong results, so order them on one stream.
+ */
+#define LBM_NUSSELT_STATIC_MAX_FACE_NODES 1048576
+LBM_API int lbm_nusselt_static(int lattice, int nx, int ny, int nz, const int face_kind[6],
+                               const double T_wall[6], double T_ref, const void* g, int face,
+                               double L, double dT, double* result, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
             "lbm_set_populations": [H, v, v, i],
             "lbm_get_state": [H, v, s],
             "lbm_set_state": [H, v, s],
+            "lbm_nusselt_static": [i, i, i, i, ip, dp, d, v, i, d, d, v, v],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -196,6 +197,25 @@ def lbm_get_state(h, buf: np.ndarray):
 
 def lbm_set_state(h, buf: np.ndarray):
     _check(lib().lbm_set_state(h, buf.ctypes.data, buf.nbytes), h)
+
+
+NUSSELT_STATIC_MAX_FACE_NODES = 1048576
+
+
+def lbm_nusselt_static(lattice: int, nx: int, ny: int, nz: int, face_kind, T_wall, T_ref: float,
+                       g_ptr: int, face: int, L: float, dT: float, result_ptr: int, stream: int = 0):
+    """The allocation-free Nusselt reduction: populations and the 5-double result are device
+    buffers the caller owns (see include/lbm.h)."""
+    fk = (ctypes.c_int * 6)(*face_kind)
+    tw = (ctypes.c_double * 6)(*T_wall)
+    st = lib().lbm_nusselt_static(lattice, nx, ny, nz, fk, tw, T_ref, ctypes.c_void_p(g_ptr), face,
+                                  L, dT, ctypes.c_void_p(result_ptr), ctypes.c_void_p(stream))
+    if st != LBM_OK:
+        ax = face // 2 if 0 <= face < 6 else 0
+        n_face = [ny * nz, nx * nz, nx * ny][ax]
+        why = (f"face {face} has {n_face} nodes, more than {NUSSELT_STATIC_MAX_FACE_NODES}"
+               if n_face > NUSSELT_STATIC_MAX_FACE_NODES else "invalid arguments or CUDA failure")
+        raise LbmError(st, f"lbm_nusselt_static: {why}")
 
 
 def lbm_last_error(h=None) -> str:
