@@ -184,6 +184,10 @@ def run_gpu(args):
     with torch.cuda.stream(stream):
         lat = L.Lattice(w["lattice"], w["nx"], w["ny"], w["nz"], w["Ra"], w["Pr"], w["Ma"],
                         walls=walls, precision=w["precision"], stream=stream)
+    if args.block:
+        bx, by = (int(v) for v in args.block.lower().split("x"))
+        lat.set_param("block_x", bx)
+        lat.set_param("block_y", by)
     n = lat.n
     info = lat.info()
     bpn = info.bytes_per_node_update
@@ -258,7 +262,7 @@ def run_gpu(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16s": "f16 storage, f32 arithmetic"}[w["precision"]],
         "data": "synthetic (seeded initial temperature perturbation +-1e-3 of the cavity at rest)",
         "config": {"workload": "3D differentially heated cubic cavity, D3Q27 flow + D3Q15 energy, "
                                "FP32 populations, FP64 Nusselt reduction",
@@ -271,7 +275,8 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_kind": peak_kind, "kernel": "step_d3q27_kernel<StoreF32>",
-                     "launch_ms": round(step_s * 1e3, 4)},
+                     "launch_ms": round(step_s * 1e3, 4), "traffic_unit": "bytes per launch",
+                     "block": [info.block_x, info.block_y]},
         "e2e": {"value": round(e2e, 2), "unit": "MLUPS",
                 "h2d_bytes_per_step": info.state_bytes / args.steps,
                 "d2h_bytes_per_step": (8 * n + 80) / args.steps,
@@ -388,13 +393,15 @@ def main(argv=None):
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--block", default=None, help="thread-block shape of the step, e.g. 128x1")
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "fp16s"])
     ap.add_argument("--nx", type=int, default=None, help="override the box (profiling cases)")
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    for k in ("nx", "ny", "nz"):
+    for k in ("nx", "ny", "nz", "precision"):
         if getattr(args, k) is not None:
             WORKLOAD[k] = getattr(args, k)
     line = run_reference(args) if args.impl == "reference" else run_gpu(args)

@@ -82,6 +82,7 @@ typedef struct {
     long long steps;            /* time steps taken since creation */
     double bytes_per_node_update; /* algorithmic HBM bytes per node and step: 2 (q_f + q_g) size */
     size_t state_bytes;         /* size of an lbm_get_state checkpoint */
+    int block_x, block_y;       /* thread-block shape of the step launch */
 } lbm_info_t;
 
 /*
@@ -125,8 +126,10 @@ LBM_API int lbm_set_stream(lbm_handle h, void* stream);
  */
 LBM_API int lbm_set_omegas(lbm_handle h, const double* om_f, int n_f, const double* om_g, int n_g);
 
-/* Set a scalar parameter: "gbeta", "T_ref", "omega_nu", "omega_alpha", "omega_bulk".
- * Errors: LBM_EINVAL for an unknown key or a rate outside (0, 2). */
+/* Set a scalar parameter: "gbeta", "T_ref", "omega_nu", "omega_alpha", "omega_bulk", or the
+ * thread-block shape of the step launch, "block_x" (32, 64, 128 or 256) and "block_y"
+ * (block_x * block_y <= 256).  Errors: LBM_EINVAL for an unknown key, a rate outside (0, 2) or a
+ * bad block shape. */
 LBM_API int lbm_set_param(lbm_handle h, const char* key, double value);
 LBM_API int lbm_info(lbm_handle h, lbm_info_t* out);
 

@@ -49,6 +49,7 @@ struct lbm_s {
     unsigned* ticket = nullptr;
     unsigned* status = nullptr;
     cudaStream_t stream = nullptr;
+    int block_x = 0, block_y = 0;   // launch shape of the step kernel (0: default)
     long long steps = 0;
     std::string err;
     lbm_alloc_fn alloc = nullptr;
@@ -327,6 +328,24 @@ int lbm_set_param(lbm_handle h, const char* key, double v)
 {
     if (!h || !key) return fail(h, LBM_EINVAL, "handle or key is NULL");
     const std::string k(key);
+    if (k == "block_x" || k == "block_y") {
+        const int v_i = (int)v;
+        if (v != (double)v_i || v_i < 1) return fail(h, LBM_EINVAL, "%s must be a positive integer", key);
+        const int bx = k == "block_x" ? v_i : h->block_x, by = k == "block_y" ? v_i : h->block_y;
+        if (bx != 0 && !(bx == 32 || bx == 64 || bx == 128 || bx == 256))
+            return fail(h, LBM_EINVAL, "block_x must be 32, 64, 128 or 256");
+        if (bx != 0 && by != 0 && bx * by > 256)
+            return fail(h, LBM_EINVAL, "block_x * block_y must not exceed 256 threads");
+        (k == "block_x" ? h->block_x : h->block_y) = v_i;
+        if (h->block_x && !h->block_y) h->block_y = std::max(1, 256 / h->block_x);
+        if (h->block_y && !h->block_x) h->block_x = 32;
+        if (h->block_x * h->block_y > 256) h->block_y = 256 / h->block_x;
+        if ((h->ny + h->block_y - 1) / h->block_y > 65535) {
+            h->block_x = h->block_y = 0;
+            return fail(h, LBM_EINVAL, "block_y too small for ny = %d", h->ny);
+        }
+        return LBM_OK;
+    }
     if (k == "gbeta" || k == "T_ref") {
         if (!std::isfinite(v)) return fail(h, LBM_EINVAL, "%s must be finite", key);
         (k == "gbeta" ? h->hc.gbeta : h->hc.T_ref) = v;
@@ -370,6 +389,9 @@ int lbm_info(lbm_handle h, lbm_info_t* o)
     o->steps = h->steps;
     o->bytes_per_node_update = 2.0 * (h->qf + h->qg) * (double)lbm::storage_bytes(h->prec);
     o->state_bytes = kStateHeader + pop_bytes(h);
+    const dim3 b = lbm::block_shape(h->nx, dim3(h->block_x, h->block_y, 1), h->dim);
+    o->block_x = (int)b.x;
+    o->block_y = (int)b.y;
     return LBM_OK;
 }
 
@@ -380,7 +402,8 @@ int lbm_step(lbm_handle h, long n)
     for (long t = 0; t < n; ++t) {
         const int c = h->cur;
         LBM_CK(h, lbm::launch_step(h->dim, h->prec, h->f[c], h->g[c], h->f[1 - c], h->g[1 - c],
-                                   h->geo, h->hc, h->status, h->stream));
+                                   h->geo, h->hc, h->status, dim3(h->block_x, h->block_y, 1),
+                                   h->stream));
         h->cur = 1 - c;
         ++h->steps;
     }

@@ -11,13 +11,14 @@ size_t storage_bytes(int prec)
 }
 
 cudaError_t launch_step(int dim, int prec, const void* fin, const void* gin, void* fout, void* gout,
-                        const Geometry& geo, const HostCoeffs& hc, unsigned* status, cudaStream_t st)
+                        const Geometry& geo, const HostCoeffs& hc, unsigned* status, dim3 block,
+                        cudaStream_t st)
 {
-    if (dim == 2) return launch_step_d2q9(prec, fin, gin, fout, gout, geo, hc, status, st);
+    if (dim == 2) return launch_step_d2q9(prec, fin, gin, fout, gout, geo, hc, status, block, st);
     switch (prec) {
-    case kF64: return launch_step_d3q27_f64(fin, gin, fout, gout, geo, hc, status, st);
-    case kF32: return launch_step_d3q27_f32(fin, gin, fout, gout, geo, hc, status, st);
-    case kF16S: return launch_step_d3q27_f16s(fin, gin, fout, gout, geo, hc, status, st);
+    case kF64: return launch_step_d3q27_f64(fin, gin, fout, gout, geo, hc, status, block, st);
+    case kF32: return launch_step_d3q27_f32(fin, gin, fout, gout, geo, hc, status, block, st);
+    case kF16S: return launch_step_d3q27_f16s(fin, gin, fout, gout, geo, hc, status, block, st);
     }
     return cudaErrorInvalidValue;
 }

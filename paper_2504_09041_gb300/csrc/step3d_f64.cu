@@ -7,12 +7,12 @@ namespace lbm {
 
 cudaError_t launch_step_d3q27_f64(const void* fin, const void* gin, void* fout, void* gout,
                                   const Geometry& geo, const HostCoeffs& hc, unsigned* status,
-                                  cudaStream_t st)
+                                  dim3 block, cudaStream_t st)
 {
     using S = StoreF64;
     using T = typename S::T;
     using R = typename S::R;
-    const dim3 b = block_shape(geo.nx);
+    const dim3 b = block_shape(geo.nx, block, 3);
     const auto c = make_coeffs<R, 27, 15>(hc);
     if (index32(geo, 27))
         step_d3q27_kernel<S, unsigned><<<grid_shape(geo, b), b, 0, st>>>(

@@ -18,6 +18,10 @@
 #include "lattices.cuh"
 #include "lbm_common.cuh"
 
+#ifndef LBM_MINB3D
+#define LBM_MINB3D Launch3D<S>::kMinBlocks
+#endif
+
 namespace lbm {
 
 template <class R>
@@ -403,7 +407,7 @@ struct Launch3D {
 };
 
 template <class S, class Idx>
-__global__ void __launch_bounds__(256, Launch3D<S>::kMinBlocks)
+__global__ void __launch_bounds__(256, LBM_MINB3D)
     step_d3q27_kernel(const typename S::T* __restrict__ fin, const typename S::T* __restrict__ gin,
                       typename S::T* __restrict__ fout, typename S::T* __restrict__ gout,
                       Geometry geo, Coeffs3D<typename S::R> c, unsigned* status)

@@ -47,7 +47,7 @@ class lbm_info_t(ctypes.Structure):
                 ("gbeta", ctypes.c_double), ("T_ref", ctypes.c_double),
                 ("om_f", ctypes.c_double * 27), ("om_g", ctypes.c_double * 15),
                 ("steps", ctypes.c_longlong), ("bytes_per_node_update", ctypes.c_double),
-                ("state_bytes", ctypes.c_size_t)]
+                ("state_bytes", ctypes.c_size_t), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
