@@ -233,9 +233,10 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t_e2e = reduce_max(time.perf_counter() - t0, world)
 
-    forms = []
+    forms, adjoint = [], None
     if world == 1 and not args.no_forms:
         forms = measure_forms(L, torch, stream, args)
+        adjoint = measure_adjoint(L, torch, stream)
 
     clk = clocks.summary()
     lat.close()
@@ -288,6 +289,8 @@ def run_gpu(args):
     }
     if forms:
         line["per_form"] = forms
+    if adjoint:
+        line["adjoint"] = adjoint
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     return line
@@ -321,6 +324,57 @@ def measure_forms(L, torch, stream, args):
                     "hbm_frac": round(gbs / peak, 4), "steps": k})
         lat.close()
     return out
+
+
+def measure_adjoint(L, torch, stream):
+    """The adjoint workload: 256^2 cavity, Ra 1e5, 2000 steps, gradient of the mean cold-wall Nu
+    with respect to the 256-node hot-wall profile; FP32 forward, FP64 adjoint.  Reports the time
+    per forward step and per adjoint step (the whole lbm_adjoint_step call, checkpointed forward,
+    segment recomputation and adjoint kernels, divided by the step count)."""
+    import numpy as np
+    import math
+    n, steps = 256, 2000
+    rng = np.random.default_rng(2024)
+    a = rng.uniform(-1.0, 1.0, 4)
+    j = np.arange(n) + 0.5
+    prof = 1.0 + 0.05 * sum(a[k] * np.sin(math.pi * (k + 1) * j / n) for k in range(4))
+    lat = L.Lattice("d2q9", n, n, 1, 1e5, 0.71, 0.1, walls=L.Walls.cavity(2), precision="fp32",
+                    stream=stream)
+    lat.set_wall_profile(0, prof)
+    state0 = lat.get_state()
+    lat.step(20)
+    lat.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat.set_state(state0)
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1) / 1e3
+    timings = {}
+    for flag in (1, 0):
+        lat.set_param("adjoint_fp64", flag)
+        lat.set_state(state0)
+        lat.adjoint(50, 1, 0)          # warm-up of the adjoint path
+        lat.set_state(state0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, grad = lat.adjoint(steps, 1, 0)
+        timings[flag] = (time.perf_counter() - t0, J, grad)
+    lat.close()
+    adj, J, grad = timings[1]
+    adj32 = timings[0][0]
+    return {"workload": "2D cavity 256x256, Ra 1e5, Pr 0.71, 2000 steps, dJ/dT_w of the mean "
+                        "cold-wall Nu w.r.t. the 256-node hot-wall profile",
+            "forward_ms_per_step": round(fwd / steps * 1e3, 5),
+            "adjoint_ms_per_step": round(adj / steps * 1e3, 5),
+            "adjoint_over_forward": round(adj / fwd, 3),
+            "fp32_arithmetic": {"adjoint_ms_per_step": round(adj32 / steps * 1e3, 5),
+                                "adjoint_over_forward": round(adj32 / fwd, 3)},
+            "arithmetic": "FP32 forward states, FP64 vector-Jacobian products and accumulation",
+            "J": J,
+            "grad_norm": float(np.linalg.norm(grad)),
+            "checkpoints": int(math.ceil(math.sqrt(steps)))}
 
 
 # ---------------------------------------------------------------------------------------------

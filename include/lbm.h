@@ -83,6 +83,7 @@ typedef struct {
     double bytes_per_node_update; /* algorithmic HBM bytes per node and step: 2 (q_f + q_g) size */
     size_t state_bytes;         /* size of an lbm_get_state checkpoint */
     int block_x, block_y;       /* thread-block shape of the step launch */
+    int graph_steps;            /* steps per CUDA graph replayed by lbm_step (0: plain launches) */
 } lbm_info_t;
 
 /*
@@ -126,7 +127,9 @@ LBM_API int lbm_set_stream(lbm_handle h, void* stream);
  */
 LBM_API int lbm_set_omegas(lbm_handle h, const double* om_f, int n_f, const double* om_g, int n_g);
 
-/* Set a scalar parameter: "gbeta", "T_ref", "omega_nu", "omega_alpha", "omega_bulk", or the
+/* Set a scalar parameter: "gbeta", "T_ref", "omega_nu", "omega_alpha", "omega_bulk",
+ * "adjoint_fp64" (0 or 1: arithmetic of lbm_adjoint_step's vector-Jacobian products),
+ * "graph_steps" (even count of steps that lbm_step replays as one CUDA graph; 0 disables), or the
  * thread-block shape of the step launch, "block_x" (32, 64, 128 or 256) and "block_y"
  * (block_x * block_y <= 256).  Errors: LBM_EINVAL for an unknown key, a rate outside (0, 2) or a
  * bad block shape. */
@@ -134,7 +137,9 @@ LBM_API int lbm_set_param(lbm_handle h, const char* key, double value);
 LBM_API int lbm_info(lbm_handle h, lbm_info_t* out);
 
 /*
- * Advance n >= 0 time steps (asynchronous on the handle's stream): per step one fused launch that
+ * Advance n >= 0 time steps (asynchronous on the handle's stream).  Runs of graph_steps steps (32 by
+ * default) are replayed from a CUDA graph captured once per buffer parity and launch settings;
+ * the rest are plain launches.  Per step one fused launch that
  * pulls the post-collision populations along every link with the wall rules of Sec. 5.1, forms
  * T = sum g, F = g beta (T - T_o) along gravity, rho = sum f, rho u = sum f e + F/2 (App. A Step 7),
  * and relaxes f and g in central-moment space (App. A/B/C Steps 1-5).
@@ -171,6 +176,24 @@ LBM_API int lbm_nusselt_profile(lbm_handle h, int face, double* nu, long n, int 
 /* Per-node wall temperature of a fixed-T face (n = face nodes, tangential order as above, host
  * pointer); T_w = NULL returns the face to its uniform T_wall.  Errors: LBM_EINVAL. */
 LBM_API int lbm_set_wall_profile(lbm_handle h, int face, const double* T_w, long n);
+
+/*
+ * Reverse-mode gradient of a wall Nusselt objective with respect to a wall-temperature profile.
+ * J = the mean Nu on objective_face (as lbm_nusselt) after n_steps >= 1 steps from the current
+ * state; grad_Tw[j] = dJ/dT_w(j) for every node j of design_face (a fixed-T face other than
+ * objective_face; tangential order as in lbm_set_wall_profile).  The call runs the n_steps forward
+ * (the handle ends at that state, as after lbm_step), keeping a checkpoint every
+ * K = ceil(sqrt(n_steps)) steps, then n_steps fused adjoint steps backward, recomputing each
+ * segment of K states once from its checkpoint: about 2 sqrt(n_steps) states of device memory and
+ * one extra forward pass.  The vector-Jacobian products of the collision are evaluated at the
+ * stored states in FP64 (lbm_set_param "adjoint_fp64" = 0 selects FP32 arithmetic: about 6 times
+ * faster, gradients to about 1e-4 relative after 2000 steps); the design gradient is always
+ * accumulated in FP64.  2D (D2Q9 pair) only.
+ * J and grad_Tw are host pointers; n must equal the number of design-face nodes.
+ * Errors: LBM_EINVAL (bad faces, n, n_steps), LBM_ENOTSUP (3D), LBM_ENOMEM, LBM_ECUDA.
+ */
+LBM_API int lbm_adjoint_step(lbm_handle h, long n_steps, int objective_face, int design_face,
+                             double* J, double* grad_Tw, long n);
 
 /*
  * The stored state is the post-collision populations of the last step (before streaming).

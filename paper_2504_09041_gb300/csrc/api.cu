@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "kernels.h"
@@ -50,6 +51,13 @@ struct lbm_s {
     unsigned* status = nullptr;
     cudaStream_t stream = nullptr;
     int block_x = 0, block_y = 0;   // launch shape of the step kernel (0: default)
+    int adjoint_fp64 = 1;           // arithmetic of the adjoint's vector-Jacobian products
+    // CUDA graphs of graph_steps consecutive steps (even, so the A/B parity returns), one per
+    // starting parity, rebuilt whenever a launch parameter changes (gen != graph_gen)
+    int graph_steps = 32;
+    unsigned gen = 1, graph_gen[2] = {0, 0};
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaStream_t capture_stream = nullptr;
     long long steps = 0;
     std::string err;
     lbm_alloc_fn alloc = nullptr;
@@ -90,6 +98,9 @@ void release(lbm_s* h)
 {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    for (int k = 0; k < 2; ++k)
+        if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     for (int k = 0; k < 2; ++k) {
         dev_free(h, h->f[k]);
         dev_free(h, h->g[k]);
@@ -307,6 +318,7 @@ int lbm_set_stream(lbm_handle h, void* stream)
 {
     if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
     h->stream = (cudaStream_t)stream;
+    ++h->gen;
     return LBM_OK;
 }
 
@@ -321,6 +333,7 @@ int lbm_set_omegas(lbm_handle h, const double* om_f, int n_f, const double* om_g
         if (!rate_ok(om_g[b])) return fail(h, LBM_EINVAL, "energy rate %d = %g outside (0, 2)", b, om_g[b]);
     for (int a = 0; om_f && a < n_f; ++a) h->hc.om_f[a] = om_f[a];
     for (int b = 0; om_g && b < n_g; ++b) h->hc.om_g[b] = om_g[b];
+    ++h->gen;
     return LBM_OK;
 }
 
@@ -328,6 +341,13 @@ int lbm_set_param(lbm_handle h, const char* key, double v)
 {
     if (!h || !key) return fail(h, LBM_EINVAL, "handle or key is NULL");
     const std::string k(key);
+    ++h->gen;
+    if (k == "graph_steps") {
+        const int v_i = (int)v;
+        if (v != (double)v_i || v_i < 0 || v_i > 4096) return fail(h, LBM_EINVAL, "graph_steps must be an integer in [0, 4096]");
+        h->graph_steps = v_i + (v_i & 1);
+        return LBM_OK;
+    }
     if (k == "block_x" || k == "block_y") {
         const int v_i = (int)v;
         if (v != (double)v_i || v_i < 1) return fail(h, LBM_EINVAL, "%s must be a positive integer", key);
@@ -344,6 +364,11 @@ int lbm_set_param(lbm_handle h, const char* key, double v)
             h->block_x = h->block_y = 0;
             return fail(h, LBM_EINVAL, "block_y too small for ny = %d", h->ny);
         }
+        return LBM_OK;
+    }
+    if (k == "adjoint_fp64") {
+        if (!(v == 0.0 || v == 1.0)) return fail(h, LBM_EINVAL, "adjoint_fp64 must be 0 or 1");
+        h->adjoint_fp64 = (int)v;
         return LBM_OK;
     }
     if (k == "gbeta" || k == "T_ref") {
@@ -392,6 +417,36 @@ int lbm_info(lbm_handle h, lbm_info_t* o)
     const dim3 b = lbm::block_shape(h->nx, dim3(h->block_x, h->block_y, 1), h->dim);
     o->block_x = (int)b.x;
     o->block_y = (int)b.y;
+    o->graph_steps = h->graph_steps;
+    return LBM_OK;
+}
+
+// Capture graph_steps steps starting from buffer parity `par` into h->graph[par].
+static int build_graph(lbm_s* h, int par)
+{
+    if (!h->capture_stream) LBM_CK(h, cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+    if (h->graph[par]) {
+        LBM_CK(h, cudaGraphExecDestroy(h->graph[par]));
+        h->graph[par] = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    LBM_CK(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    int c = par;
+    for (int t = 0; t < h->graph_steps && e == cudaSuccess; ++t) {
+        e = lbm::launch_step(h->dim, h->prec, h->f[c], h->g[c], h->f[1 - c], h->g[1 - c], h->geo, h->hc,
+                             h->status, dim3(h->block_x, h->block_y, 1), h->capture_stream);
+        c = 1 - c;
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(h, LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&h->graph[par], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "graph instantiation: %s", cudaGetErrorString(e));
+    h->graph_gen[par] = h->gen;
     return LBM_OK;
 }
 
@@ -399,6 +454,17 @@ int lbm_step(lbm_handle h, long n)
 {
     if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
     if (n < 0) return fail(h, LBM_EINVAL, "negative step count %ld", n);
+    // whole graphs of graph_steps steps, then single launches
+    while (h->graph_steps > 0 && n >= h->graph_steps) {
+        const int par = h->cur;
+        if (!h->graph[par] || h->graph_gen[par] != h->gen) {
+            const int rc = build_graph(h, par);
+            if (rc) return rc;
+        }
+        LBM_CK(h, cudaGraphLaunch(h->graph[par], h->stream));
+        h->steps += h->graph_steps;
+        n -= h->graph_steps;
+    }
     for (long t = 0; t < n; ++t) {
         const int c = h->cur;
         LBM_CK(h, lbm::launch_step(h->dim, h->prec, h->f[c], h->g[c], h->f[1 - c], h->g[1 - c],
@@ -502,6 +568,7 @@ int lbm_set_wall_profile(lbm_handle h, int face, const double* T_w, long n)
         dev_free(h, h->profile[face]);
         h->profile[face] = nullptr;
         h->geo.profile[face] = nullptr;
+        ++h->gen;
         return LBM_OK;
     }
     if (n != face_nodes(h, face)) return fail(h, LBM_EINVAL, "face %d has %ld nodes, not %ld", face, face_nodes(h, face), n);
@@ -514,6 +581,113 @@ int lbm_set_wall_profile(lbm_handle h, int face, const double* T_w, long n)
     LBM_CK(h, cudaMemcpyAsync(h->profile[face], T_w, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     LBM_CK(h, cudaStreamSynchronize(h->stream));
     h->geo.profile[face] = h->profile[face];
+    ++h->gen;
+    return LBM_OK;
+}
+
+int lbm_adjoint_step(lbm_handle h, long n_steps, int objective_face, int design_face, double* J,
+                     double* grad_Tw, long n)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+    if (h->dim != 2) return fail(h, LBM_ENOTSUP, "the adjoint step is implemented for the D2Q9 pair");
+    if (n_steps < 1) return fail(h, LBM_EINVAL, "n_steps must be at least 1");
+    if (!J || !grad_Tw) return fail(h, LBM_EINVAL, "J or grad_Tw is NULL");
+    for (int f : {objective_face, design_face})
+        if (f < 0 || f >= 4 || h->geo.kind[f] != LBM_WALL_FIXED_T)
+            return fail(h, LBM_EINVAL, "face %d is not a fixed-temperature wall of this box", f);
+    if (objective_face == design_face) return fail(h, LBM_EINVAL, "objective and design face must differ");
+    const int ext[2] = {h->nx, h->ny};
+    if (ext[objective_face / 2] < 3) return fail(h, LBM_EINVAL, "fewer than three node layers normal to the objective face");
+    if (n != face_nodes(h, design_face)) return fail(h, LBM_EINVAL, "design face %d has %ld nodes, not %ld", design_face, face_nodes(h, design_face), n);
+
+    const size_t sb = lbm::storage_bytes(h->prec);
+    const size_t fb = (size_t)h->qf * h->geo.n * sb, gb = (size_t)h->qg * h->geo.n * sb;
+    const long K = (long)std::ceil(std::sqrt((double)n_steps));
+    const long nck = (n_steps + K - 1) / K;
+    // device memory: nck checkpoints, K - 1 segment states, two adjoint buffers, the gradient
+    std::vector<void*> ckf(nck, nullptr), ckg(nck, nullptr), sgf(K, nullptr), sgg(K, nullptr);
+    void* mu[2] = {nullptr, nullptr};
+    double* grad = nullptr;
+    const bool afp64 = h->adjoint_fp64 != 0;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(h->stream);
+        for (auto p : ckf) dev_free(h, p);
+        for (auto p : ckg) dev_free(h, p);
+        for (auto p : sgf) dev_free(h, p);
+        for (auto p : sgg) dev_free(h, p);
+        dev_free(h, mu[0]);
+        dev_free(h, mu[1]);
+        dev_free(h, grad);
+    };
+    bool ok = true;
+    for (long m = 0; m < nck && ok; ++m) ok = (ckf[m] = dev_alloc(h, fb)) && (ckg[m] = dev_alloc(h, gb));
+    for (long r = 1; r < K && ok; ++r) ok = (sgf[r] = dev_alloc(h, fb)) && (sgg[r] = dev_alloc(h, gb));
+    const size_t mub = (size_t)(h->qf + h->qg) * h->geo.n * (afp64 ? sizeof(double) : sizeof(float));
+    ok = ok && (mu[0] = dev_alloc(h, mub)) && (mu[1] = dev_alloc(h, mub)) &&
+         (grad = (double*)dev_alloc(h, sizeof(double) * n));
+    if (!ok) {
+        cleanup();
+        return fail(h, LBM_ENOMEM, "no device memory for %ld checkpoints of the adjoint", nck + K);
+    }
+#define ADJ_CK(expr)                                                                                \
+    do {                                                                                            \
+        cudaError_t e_ = (expr);                                                                    \
+        if (e_ != cudaSuccess) {                                                                    \
+            cleanup();                                                                              \
+            return fail(h, LBM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));                    \
+        }                                                                                           \
+    } while (0)
+    const dim3 blk(h->block_x, h->block_y, 1);
+    // forward pass with checkpoints s_0, s_K, s_2K, ...
+    ADJ_CK(cudaMemcpyAsync(ckf[0], h->f[h->cur], fb, cudaMemcpyDeviceToDevice, h->stream));
+    ADJ_CK(cudaMemcpyAsync(ckg[0], h->g[h->cur], gb, cudaMemcpyDeviceToDevice, h->stream));
+    for (long k = 1; k <= n_steps; ++k) {
+        const int c = h->cur;
+        ADJ_CK(lbm::launch_step(h->dim, h->prec, h->f[c], h->g[c], h->f[1 - c], h->g[1 - c], h->geo,
+                                h->hc, h->status, blk, h->stream));
+        h->cur = 1 - c;
+        ++h->steps;
+        if (k % K == 0 && k / K < nck) {
+            ADJ_CK(cudaMemcpyAsync(ckf[k / K], h->f[h->cur], fb, cudaMemcpyDeviceToDevice, h->stream));
+            ADJ_CK(cudaMemcpyAsync(ckg[k / K], h->g[h->cur], gb, cudaMemcpyDeviceToDevice, h->stream));
+        }
+    }
+    // objective at the final state
+    const double sgn = h->geo.T_wall[objective_face] >= h->hc.T_ref ? 1.0 : -1.0;
+    const double scale = -sgn * h->L / h->dT;
+    ADJ_CK(lbm::launch_nusselt(h->dim, h->prec, h->f[h->cur], h->g[h->cur], h->geo, h->hc, objective_face,
+                               scale, h->nu_profile, h->nu_scratch, h->ticket, h->nu_result, h->stream));
+    double r[5];
+    ADJ_CK(cudaMemcpyAsync(r, h->nu_result, sizeof r, cudaMemcpyDeviceToHost, h->stream));
+    // seed mu_{n+1} = dJ/dp_{n+1}
+    int a = 0;
+    ADJ_CK(cudaMemsetAsync(mu[a], 0, mub, h->stream));
+    ADJ_CK(cudaMemsetAsync(grad, 0, sizeof(double) * n, h->stream));
+    ADJ_CK(lbm::launch_adjoint_seed(h->geo, objective_face, scale, mu[a], afp64, h->stream));
+    // backward over the segments, last first
+    for (long m = nck - 1; m >= 0; --m) {
+        const long lo = m * K, hi = std::min((m + 1) * K, n_steps);
+        std::vector<const void*> sf(hi - lo), sg(hi - lo);
+        sf[0] = ckf[m];
+        sg[0] = ckg[m];
+        for (long r2 = 1; r2 < hi - lo; ++r2) {
+            ADJ_CK(lbm::launch_step(h->dim, h->prec, sf[r2 - 1], sg[r2 - 1], sgf[r2], sgg[r2], h->geo,
+                                    h->hc, h->status, blk, h->stream));
+            sf[r2] = sgf[r2];
+            sg[r2] = sgg[r2];
+        }
+        for (long k = hi; k >= lo + 1; --k) {
+            ADJ_CK(lbm::launch_adjoint_step_d2q9(h->prec, afp64, sf[k - 1 - lo], sg[k - 1 - lo], mu[a],
+                                                 mu[1 - a], h->geo, h->hc, design_face, grad,
+                                                 h->stream));
+            a = 1 - a;
+        }
+    }
+    ADJ_CK(cudaMemcpyAsync(grad_Tw, grad, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    ADJ_CK(cudaStreamSynchronize(h->stream));
+#undef ADJ_CK
+    *J = r[0] / (double)face_nodes(h, objective_face);
+    cleanup();
     return LBM_OK;
 }
 

@@ -56,6 +56,17 @@ cudaError_t launch_nusselt(int dim, int prec, const void* f, const void* g, cons
                            const HostCoeffs& hc, int face, double scale, double* profile,
                            double* scratch, unsigned* ticket, double* result, cudaStream_t st);
 
+// Adjoint of the D2Q9 step (adjoint_d2q9.cuh): seed mu_{n+1} = dJ/dp for J = mean Nu on `face`
+// (mu must be zeroed first), and one fused adjoint step mu_{k+1} -> mu_k from the state s_{k-1},
+// adding the design-face wall-temperature gradient (FP64) to grad.  mu holds FP64 values when
+// fp64 is set, FP32 otherwise.
+cudaError_t launch_adjoint_seed(const Geometry& geo, int face, double scale, void* mu, bool fp64,
+                                cudaStream_t st);
+cudaError_t launch_adjoint_step_d2q9(int prec, bool fp64, const void* f_prev, const void* g_prev,
+                                     const void* mu_in, void* mu_out, const Geometry& geo,
+                                     const HostCoeffs& hc, int design_face, double* grad,
+                                     cudaStream_t st);
+
 }  // namespace lbm
 
 namespace lbm {

@@ -47,7 +47,8 @@ class lbm_info_t(ctypes.Structure):
                 ("gbeta", ctypes.c_double), ("T_ref", ctypes.c_double),
                 ("om_f", ctypes.c_double * 27), ("om_g", ctypes.c_double * 15),
                 ("steps", ctypes.c_longlong), ("bytes_per_node_update", ctypes.c_double),
-                ("state_bytes", ctypes.c_size_t), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int)]
+                ("state_bytes", ctypes.c_size_t), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
+                ("graph_steps", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -86,6 +87,7 @@ def lib() -> ctypes.CDLL:
             "lbm_get_state": [H, v, s],
             "lbm_set_state": [H, v, s],
             "lbm_nusselt_static": [i, i, i, i, ip, dp, d, v, i, d, d, v, v],
+            "lbm_adjoint_step": [H, ctypes.c_long, i, i, dp, dp, ctypes.c_long],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -197,6 +199,15 @@ def lbm_get_state(h, buf: np.ndarray):
 
 def lbm_set_state(h, buf: np.ndarray):
     _check(lib().lbm_set_state(h, buf.ctypes.data, buf.nbytes), h)
+
+
+def lbm_adjoint_step(h, n_steps: int, objective_face: int, design_face: int, n: int):
+    """(J, dJ/dT_w) for J = mean Nu on objective_face after n_steps, T_w the design-face profile."""
+    J = ctypes.c_double()
+    grad = np.zeros(n)
+    _check(lib().lbm_adjoint_step(h, n_steps, objective_face, design_face, ctypes.byref(J),
+                                  _dptr(grad.ctypes.data), n), h)
+    return J.value, grad
 
 
 NUSSELT_STATIC_MAX_FACE_NODES = 1048576
@@ -361,6 +372,14 @@ class Lattice:
     def set_wall_profile(self, face: int, T_w):
         lbm_set_wall_profile(self.h, face, T_w)
 
+    def face_nodes(self, face: int) -> int:
+        return {0: self.ny * self.nz, 1: self.nx * self.nz, 2: self.nx * self.ny}[face // 2]
+
+    def adjoint(self, n_steps: int, objective_face: int, design_face: int):
+        """J and dJ/dT_w (numpy) by the checkpointed adjoint; the state advances n_steps."""
+        return lbm_adjoint_step(self.h, n_steps, objective_face, design_face,
+                                self.face_nodes(design_face))
+
     def get_populations(self, device: bool = False):
         """Post-collision state as FP64 arrays (q, nz, ny, nx): numpy, or torch on the device."""
         t = self.torch
@@ -391,3 +410,27 @@ class Lattice:
 
     def set_state(self, buf: np.ndarray):
         lbm_set_state(self.h, np.ascontiguousarray(buf, dtype=np.uint8))
+
+
+def wall_nusselt_objective(lattice: "Lattice", state0, n_steps: int, objective_face: int,
+                           design_face: int):
+    """A torch function T_w -> J: the mean Nusselt number on objective_face after n_steps steps
+    from the checkpoint state0, as a differentiable function of the design-face temperatures.
+    Its backward is the library's adjoint (lbm_adjoint_step)."""
+    import torch
+
+    class _WallNusselt(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, T_w):
+            lattice.set_state(state0)
+            lattice.set_wall_profile(design_face, T_w.detach().cpu().double().numpy())
+            J, grad = lattice.adjoint(n_steps, objective_face, design_face)
+            ctx.save_for_backward(torch.from_numpy(grad).to(T_w.device, T_w.dtype))
+            return torch.tensor(J, dtype=T_w.dtype, device=T_w.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            (grad,) = ctx.saved_tensors
+            return gJ * grad
+
+    return _WallNusselt.apply

@@ -446,3 +446,24 @@ def test_cubic_cavity_128_matches_table_compare_nu3d(Ra, steps):
     key = {1e5: "1e5", 1e6: "1e6"}[Ra]
     assert hot == pytest.approx(gold["nu_mean_3d"][key], rel=0.01)
     assert cold == pytest.approx(hot, rel=2e-3)
+
+
+@pytest.mark.parametrize("dim,shape", [(2, (1, 40, 70)), (3, (9, 12, 20))])
+def test_graph_replay_equals_plain_launches(dim, shape):
+    """lbm_step replays runs of graph_steps steps from a CUDA graph; the state must be bit-for-bit
+    the one of plain launches, also after a parameter change invalidates the graph."""
+    nz, ny, nx = shape
+    lat = "d2q9" if dim == 2 else "d3q27"
+    a = L.Lattice(lat, nx, ny, nz, Ra=1e5, walls=L.Walls.cavity(dim), precision="fp32")
+    b = L.Lattice(lat, nx, ny, nz, Ra=1e5, walls=L.Walls.cavity(dim), precision="fp32")
+    b.set_param("graph_steps", 0)
+    assert a.info().graph_steps == 32 and b.info().graph_steps == 0
+    for lt in (a, b):
+        lt.step(77)
+        lt.set_param("gbeta", 2.5e-3)
+        lt.step(45)
+        lt.sync()
+    fa, ga = a.get_populations()
+    fb, gb = b.get_populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    assert a.info().steps == b.info().steps == 122
