@@ -11,19 +11,19 @@
  *   - D2Q9 flow collision .......... Appendix A, Steps 1-5 (Step 7 for rho, u)
  *   - D2Q9 energy collision ........ Appendix B, Steps 1-5
  *   - D3Q15 energy collision ....... Appendix C, Steps 1-5
- *   - D3Q27 flow collision ......... Sec. 4.2 (moment definitions, attractors, forcing, Eq. forcing:3D);
+ *   - D3Q27 flow collision ......... Sec. 5.1-5.2 (moment definitions, attractors, Eq. forcing:3D);
  *                                    the full algorithm is deferred by the paper to its earlier work,
  *                                    so the reading used here is stated at orc_d3q27_collide.
- *   - streaming and walls .......... Eqs. LBMsteps-stream / LBMsteps-streamg, Sec. 5.1 (half-way
- *                                    bounce-back, anti-bounce-back), Boussinesq force Sec. 5.1 / 5.2
- *   - wall Nusselt number .......... Sec. 5.1 (second-order one-sided Lagrange derivative)
+ *   - streaming and walls .......... Eqs. LBMsteps-stream / LBMsteps-streamg, Sec. 6.1 (half-way
+ *                                    bounce-back, anti-bounce-back), Boussinesq force Sec. 6.1 / 6.2
+ *   - wall Nusselt number .......... Sec. 6.1 (second-order one-sided Lagrange derivative)
  *
  * Readings of garbled or silent passages (each also checked by a test):
  *   R1  App. A Step 2, kappa_22: the term printed "u_x^2 2 u_y kappa'_01" is -2 u_x^2 u_y kappa'_01.
  *   R2  App. B Step 2, eta_12: the printed kappa'_11 is eta'_11.
- *   R3  App. C Step 3 / Sec. 4.4: eta^Mv_012 = (2/3) c_s^2-hat eta~_010 (the factor c_s^2-hat is
- *       dropped once in Sec. 4.4 and present in App. C and in the recurrence).
- *   R4  Sec. 4.2 discrete kappa^Mv_122: the product "kappa~_011 kappa~_012" is kappa~_110 kappa~_012
+ *   R3  App. C Step 3 / Sec. 5.4: eta^Mv_012 = (2/3) c_s^2-hat eta~_010 (the factor c_s^2-hat is
+ *       dropped once in Sec. 5.4 and present in App. C and in the recurrence).
+ *   R4  Sec. 5.2 discrete kappa^Mv_122: the product "kappa~_011 kappa~_012" is kappa~_110 kappa~_012
  *       (continuous form of the same attractor and the recurrence Eq. Mvcmattractor3D).
  *   R5  Second-order sources are zero (Eq. sourceCM2D states sigma_20 = sigma_02 = sigma_11 = 0);
  *       higher-order sources use the pre-collision central moments.
@@ -62,20 +62,20 @@ static const int D2Q9_E[9][3] = {
     {0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0},
     {1, 1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
 
-/* D3Q27, Sec. 4.2 (Cartesian components of the 27 links). */
+/* D3Q27, Sec. 5.2 (Cartesian components of the 27 links). */
 static const int D3Q27_E[27][3] = {
     {0, 0, 0},   {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},  {0, 0, 1},   {0, 0, -1},
     {1, 1, 0},   {-1, 1, 0},  {1, -1, 0},  {-1, -1, 0}, {1, 0, 1},   {-1, 0, 1},  {1, 0, -1},
     {-1, 0, -1}, {0, 1, 1},   {0, -1, 1},  {0, 1, -1},  {0, -1, -1}, {1, 1, 1},   {-1, 1, 1},
     {1, -1, 1},  {-1, -1, 1}, {1, 1, -1},  {-1, 1, -1}, {1, -1, -1}, {-1, -1, -1}};
 
-/* D3Q15, Sec. 4.4. */
+/* D3Q15, Sec. 5.4. */
 static const int D3Q15_E[15][3] = {
     {0, 0, 0},  {1, 0, 0},  {-1, 0, 0},  {0, 1, 0},  {0, -1, 0},
     {0, 0, 1},  {0, 0, -1}, {1, 1, 1},   {-1, 1, 1}, {1, -1, 1},
     {-1, -1, 1}, {1, 1, -1}, {-1, 1, -1}, {1, -1, -1}, {-1, -1, -1}};
 
-/* D3Q27 central-moment order of Sec. 4.2: exponents (m, n, p) of each entry of m^c. */
+/* D3Q27 central-moment order of Sec. 5.2: exponents (m, n, p) of each entry of m^c. */
 static const int M27[27][3] = {
     {0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1},
     {2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 2, 0}, {1, 0, 2}, {2, 1, 0}, {0, 1, 2},
@@ -109,7 +109,7 @@ static double binom(int n, int k)
 
 /* ------------------------------------------------------------------------------------------ */
 /* Appendix A / B, Steps 1, 2, 4, 5 on D2Q9 (identical for f and g).                           */
-/* Moment order (00, 10, 01, 20, 02, 11, 21, 12, 22), Sec. 3.2.                                 */
+/* Moment order (00, 10, 01, 20, 02, 11, 21, 12, 22), Sec. 4.2.                                 */
 /* ------------------------------------------------------------------------------------------ */
 
 /* Step 1: raw moments m = P f. */
@@ -265,7 +265,7 @@ void orc_d2q9_g_collide(const double g[9], double ux, double uy, const double om
 
 /* ------------------------------------------------------------------------------------------ */
 /* Appendix C: D3Q15 energy collision.  Moment order (000, 100, 010, 001, 110, 101, 011, 200,   */
-/* 020, 002, 120, 012, 201, 111, 220), Sec. 4.4.                                               */
+/* 020, 002, 120, 012, 201, 111, 220), Sec. 5.4.                                               */
 /* ------------------------------------------------------------------------------------------ */
 
 /* Step 1: raw moments n = P g. */
@@ -393,7 +393,7 @@ void orc_d3q15_g_collide(const double g[15], double ux, double uy, double uz, co
 }
 
 /* ------------------------------------------------------------------------------------------ */
-/* D3Q27 flow collision (Sec. 4.1-4.2, reading R6).                                            */
+/* D3Q27 flow collision (Sec. 5.1-5.2, reading R6).                                            */
 /* ------------------------------------------------------------------------------------------ */
 
 /* Central moments by their definition: kappa_mnp = sum_a f_a (e_ax-ux)^m (e_ay-uy)^n (e_az-uz)^p. */
@@ -423,7 +423,7 @@ void orc_d3q27_raw_from_central(const double k[27], double ux, double uy, double
     }
 }
 
-/* P for D3Q27: P[j][a] = e_ax^m e_ay^n e_az^p over the 27 monomials of Sec. 4.2. */
+/* P for D3Q27: P[j][a] = e_ax^m e_ay^n e_az^p over the 27 monomials of Sec. 5.2. */
 static double P27[27][27], P27INV[27][27];
 static int P27_ready = 0;
 
@@ -502,7 +502,7 @@ void orc_d3q27_macro(const double f[27], double Fx, double Fy, double Fz, double
     out[3] = (jz + 0.5 * Fz) / rho;
 }
 
-/* Attractors of orders 4-6 (Sec. 4.2 discrete list, reading R4) from post-collision kt[]. */
+/* Attractors of orders 4-6 (Sec. 5.2 discrete list, reading R4) from post-collision kt[]. */
 void orc_d3q27_attractors_high(const double kt[27], double rho, double Mv[27])
 {
     for (int j = 0; j < 27; ++j) Mv[j] = 0.0;
@@ -528,7 +528,7 @@ void orc_d3q27_attractors_high(const double kt[27], double rho, double Mv[27])
 
 /*
  * D3Q27 flow collision, reading R6.  om[j] is the rate of the j-th entry of m^c in the order
- * of Sec. 4.2, except for the three diagonal second-order slots: om[K200] relaxes the trace
+ * of Sec. 5.2, except for the three diagonal second-order slots: om[K200] relaxes the trace
  * kappa_200 + kappa_020 + kappa_002 (bulk), om[K020] the deviator kappa_200 - kappa_020 and
  * om[K002] the deviator kappa_200 - kappa_002 (shear).  Sources follow Eq. forcing:3D with the
  * pre-collision central moments; second-order sources are zero (reading R5); delta_t = 1.
@@ -796,7 +796,7 @@ static long link_source(const orc_grid *G, int x, int y, int z, const int e[3], 
     return s[0] + (long)G->nx * (s[1] + (long)G->ny * s[2]);
 }
 
-/* Streaming step (Eqs. LBMsteps-stream, LBMsteps-streamg) with the Sec. 5.1 wall rules. */
+/* Streaming step (Eqs. LBMsteps-stream, LBMsteps-streamg) with the Sec. 6.1 wall rules. */
 static void pull_node(const orc_grid *G, int x, int y, int z, double *fo, double *go)
 {
     const long i = x + (long)G->nx * (y + (long)G->ny * z);
@@ -904,7 +904,7 @@ void orc_fields(const orc_grid *G, double *rho, double *ux, double *uy, double *
 }
 
 /*
- * Local wall Nusselt numbers on a fixed-temperature face (Sec. 5.1): the wall-normal derivative
+ * Local wall Nusselt numbers on a fixed-temperature face (Sec. 6.1): the wall-normal derivative
  * at the wall from the second-order Lagrange polynomial through the wall (x0 = 0) and the first two
  * node layers (x1 = 1/2, x2 = 3/2), dT/dn = -8/3 T_w + 3 T_1 - 1/3 T_2, with n pointing into the
  * fluid.  Nu = -sgn (L / dT) dT/dn, sgn = +1 on a face at or above T_ref (heat enters the fluid)

@@ -27,7 +27,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 PERIODIC, WALL_ADIABATIC, WALL_FIXED_T = 0, 1, 2
 
-# Velocity sets in the paper's order (Eqs. ex/ey, Sec. 4.2, Sec. 4.4).
+# Velocity sets in the paper's order (Eqs. ex/ey, Sec. 5.2, Sec. 5.4).
 E_D2Q9 = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [-1, 0, 0], [0, -1, 0],
                    [1, 1, 0], [-1, 1, 0], [-1, -1, 0], [1, -1, 0]])
 E_D3Q27 = np.array([
@@ -40,7 +40,7 @@ E_D3Q15 = np.array([
     [1, 1, 1], [-1, 1, 1], [1, -1, 1], [-1, -1, 1], [1, 1, -1], [-1, 1, -1], [1, -1, -1],
     [-1, -1, -1]])
 
-# Moment orders: D2Q9 (Sec. 3.2), D3Q27 (Sec. 4.2), D3Q15 (Sec. 4.4).
+# Moment orders: D2Q9 (Sec. 4.2), D3Q27 (Sec. 5.2), D3Q15 (Sec. 5.4).
 M_D2Q9 = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (2, 0, 0), (0, 2, 0), (1, 1, 0), (2, 1, 0),
           (1, 2, 0), (2, 2, 0)]
 M_D3Q27 = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1),
@@ -235,15 +235,15 @@ def uniform01(seed: int, i: int) -> float:
 
 
 # ----------------------------------------------------------------------------------------------
-# Problem parameters (Sec. 5.1 and App. A/B/C relaxation-rate paragraphs)
+# Problem parameters (Sec. 6.1 and App. A/B/C relaxation-rate paragraphs)
 # ----------------------------------------------------------------------------------------------
 
 @dataclass
 class Transport:
-    U: float        # characteristic velocity U_o = Ma / sqrt(3)  (Ma = sqrt(3) U_o, Sec. 6)
+    U: float        # characteristic velocity U_o = Ma / sqrt(3)  (Ma = sqrt(3) U_o, Sec. 7)
     nu: float       # kinematic viscosity
     alpha: float    # thermal diffusivity
-    gbeta: float    # g*beta with g*beta*dT*L = U_o^2 (F_o = U_o^2 / L_o, Sec. 5.1)
+    gbeta: float    # g*beta with g*beta*dT*L = U_o^2 (F_o = U_o^2 / L_o, Sec. 6.1)
     omega_nu: float     # nu = c_s^2 (1/omega - 1/2)         (App. A)
     omega_alpha: float  # alpha = c_s^2-hat (1/omega - 1/2)  (App. B, App. C)
 
@@ -262,7 +262,7 @@ def default_omegas(dim: int, omega_nu: float, omega_alpha: float, omega_bulk: fl
 
     2D f: omega_3 (bulk) = omega_bulk, omega_4 = omega_5 = omega_nu (App. A).
     2D g: omega_1 = omega_2 = omega_alpha (App. B).  3D g: omega_1..3 = omega_alpha (App. C).
-    3D f (order of Sec. 4.2): the three off-diagonal second-order moments and the two deviator
+    3D f (order of Sec. 5.2): the three off-diagonal second-order moments and the two deviator
     slots (index 8, 9) take omega_nu; the trace slot (index 7) takes omega_bulk.
     """
     if dim == 2:

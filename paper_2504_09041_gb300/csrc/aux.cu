@@ -160,7 +160,7 @@ __global__ void fields_kernel(const typename S::T* f, const typename S::T* g, Ge
 }
 
 // ---------------------------------------------------------------------------------------------
-// Wall Nusselt number (Sec. 5.1): dT/dn = -8/3 T_w + 3 T_1 - 1/3 T_2 from the wall and the first
+// Wall Nusselt number (Sec. 6.1): dT/dn = -8/3 T_w + 3 T_1 - 1/3 T_2 from the wall and the first
 // two node layers; Nu = scale * dT/dn with scale = -s L / dT.  One thread per wall node, then
 // FP64 warp-shuffle reductions of (sum, max with index, min with index), per-block partials and a
 // final pass by the last block to finish (deterministic order, ties to the lowest index).

@@ -1,7 +1,7 @@
 // lattices.cuh -- velocity sets, rest weights and the per-axis central-moment transforms.
 //
-// Velocity sets keep the paper's link order (D2Q9: Eqs. ex, ey; D3Q27: Sec. 4.2; D3Q15:
-// Sec. 4.4) so that a population plane a in HBM is the paper's f_a / g_a.
+// Velocity sets keep the paper's link order (D2Q9: Eqs. ex, ey; D3Q27: Sec. 5.2; D3Q15:
+// Sec. 5.4) so that a population plane a in HBM is the paper's f_a / g_a.
 #pragma once
 
 namespace lbm {
@@ -24,7 +24,7 @@ __host__ __device__ constexpr double w9(int a)
     return a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
 
-// D3Q27 (Sec. 4.2).
+// D3Q27 (Sec. 5.2).
 __host__ __device__ constexpr int e27(int a, int d)
 {
     constexpr int t[27][3] = {
@@ -53,7 +53,7 @@ __host__ __device__ constexpr int idx27(int ex, int ey, int ez)
     return r;
 }
 
-// D3Q15 (Sec. 4.4); its corner links 7..14 are D3Q27 links 19..26 in the same order.
+// D3Q15 (Sec. 5.4); its corner links 7..14 are D3Q27 links 19..26 in the same order.
 __host__ __device__ constexpr int e15(int a, int d)
 {
     constexpr int t[15][3] = {{0, 0, 0},   {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},

@@ -21,7 +21,7 @@ template <class R>
 using Coeffs2D = Coeffs<R, 9, 9>;
 
 // Streaming (Eqs. LBMsteps-stream, LBMsteps-streamg) with half-way bounce-back for f, and
-// bounce-back (adiabatic) or anti-bounce-back (fixed T) for g at the walls (Sec. 5.1), in
+// bounce-back (adiabatic) or anti-bounce-back (fixed T) for g at the walls (Sec. 6.1), in
 // deviations: the anti-bounce-back g_a = -g~_abar + 2 w_a T_w becomes
 // gamma_a = -gamma~_abar + 2 w_a (T_w - T_o).
 template <class S, class Idx = size_t>
@@ -144,7 +144,7 @@ __device__ __forceinline__ void from_central_d2q9(R p[3][3], R f[9], R ux, R uy)
     });
 }
 
-// One time step at one node: pull, macroscopic fields (App. A Step 7, App. B Step 7, Sec. 5.1
+// One time step at one node: pull, macroscopic fields (App. A Step 7, App. B Step 7, Sec. 6.1
 // Boussinesq force), collide f and g, store.
 template <class S, class Idx>
 __device__ __forceinline__ void node_step_d2q9(const typename S::T* __restrict__ fin,

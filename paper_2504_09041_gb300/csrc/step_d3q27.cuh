@@ -1,5 +1,5 @@
 // step_d3q27.cuh -- fused pull-stream + FP central-moment collision of the coupled D3Q27 flow
-// (Sec. 4.1-4.3) and D3Q15 energy (Appendix C) lattices, one node per thread.
+// (Sec. 5.1-5.2) and D3Q15 energy (Appendix C) lattices, one node per thread.
 //
 // D3Q27: the 27 central moments kappa_abc are produced by three sweeps of 3-link lines (x, y, z),
 // which on the tensor-product lattice equals P then F; the inverse sweeps map back.
@@ -61,7 +61,7 @@ __device__ __forceinline__ void pull_d3q27_d3q15(const typename S::T* __restrict
 }
 
 // Flow collision (reading R6 of the oracle notes) on the deviations: D[c][b][a] = kappa_abc - K_abc
-// on entry, kappa~_abc - K_abc on exit.  Rate slots follow the moment order of Sec. 4.2; slot 7
+// on entry, kappa~_abc - K_abc on exit.  Rate slots follow the moment order of Sec. 5.2; slot 7
 // relaxes the trace (bulk), slots 8 and 9 the deviators kappa_200 - kappa_020, kappa_200 - kappa_002.
 // Sources (Eq. forcing:3D) use the full pre-collision moments kappa = K + D.
 template <class R>

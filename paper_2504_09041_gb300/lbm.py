@@ -284,7 +284,7 @@ class Walls:
 
     @staticmethod
     def cavity(dim: int, T_hot: float = 1.0, T_cold: float = 0.0) -> "Walls":
-        """Hot -x, cold +x, other walls adiabatic, no slip everywhere (Sec. 5.1, Sec. 5.2)."""
+        """Hot -x, cold +x, other walls adiabatic, no slip everywhere (Sec. 6.1, Sec. 6.2)."""
         face = (LBM_WALL_FIXED_T, LBM_WALL_FIXED_T) + (LBM_WALL_ADIABATIC,) * 4
         mid = 0.5 * (T_hot + T_cold)
         return Walls(face, (T_hot, T_cold, 0, 0, 0, 0), mid, mid, 1 if dim == 2 else 2)

@@ -2,7 +2,7 @@
 
 Every check here is independent of the oracle's own formulas:
   * moments are recomputed from their definitions as sums over the printed velocity sets
-    (Sec. 3.2 discrete moment definitions; Sec. 4.2; Sec. 4.4);
+    (Sec. 4.2 discrete moment definitions; Sec. 5.2; Sec. 5.4);
   * attractors are regenerated from the recurrence (Eqs. Mvcmattractor2D, Mvcmattractor3D,
     Mvcmattractor2D_g, Mvcmattractor3Dg) with the diffusion-tensor selection rules
     (Eqs. Dij2Dselection, diffusion-tensor-parameter-3D, option A for g);
@@ -160,7 +160,7 @@ def test_d3q27_transforms_against_definitions():
 # ---------------------------------------------------------------------------------------------
 
 def test_d3q27_printed_attractors_match_recurrence():
-    """Sec. 4.2 discrete attractors of orders 4-6 equal the recurrence with D' = kt/rho.
+    """Sec. 5.2 discrete attractors of orders 4-6 equal the recurrence with D' = kt/rho.
 
     This pins reading R4 (kappa^Mv_122 uses kappa~_110 kappa~_012).
     """
@@ -402,7 +402,7 @@ def test_thermal_wave_decays_at_alpha_k2(dim):
 
 
 def test_nusselt_of_linear_profile_is_one():
-    """A linear T between half-way walls gives Nu = 1 exactly (Sec. 5.1 three-point derivative)."""
+    """A linear T between half-way walls gives Nu = 1 exactly (Sec. 6.1 three-point derivative)."""
     N, TH, TC = 12, 1.0, 0.0
     bc = O.BC(face=(O.WALL_FIXED_T, O.WALL_FIXED_T, O.PERIODIC, O.PERIODIC, 0, 0),
               T_wall=(TH, TC, 0, 0, 0, 0), T_init=0.5, T_ref=0.5)
@@ -481,12 +481,12 @@ def test_splitmix64_reference_outputs():
 
 
 def test_transport_mapping_matches_worked_numbers():
-    """Ma = sqrt(3) U_o (Sec. 6), nu = U L sqrt(Pr/Ra), omega = 1/(nu/c_s^2 + 1/2) (App. A)."""
+    """Ma = sqrt(3) U_o (Sec. 7), nu = U L sqrt(Pr/Ra), omega = 1/(nu/c_s^2 + 1/2) (App. A)."""
     tr = O.transport(1e4, 0.71, 0.1, 64)
     assert tr.U == pytest.approx(0.1 / math.sqrt(3))
     assert tr.nu == pytest.approx(0.0311351, rel=1e-5)
     assert tr.omega_nu == pytest.approx(1.685186, rel=1e-5)
     assert tr.alpha == pytest.approx(tr.nu / 0.71)
     assert tr.gbeta * 1.0 * 64 == pytest.approx(tr.U ** 2)
-    # Ra recovered from the definition of Sec. 5.1
+    # Ra recovered from the definition of Sec. 6.1
     assert tr.gbeta * 1.0 * 64 ** 3 / (tr.alpha * tr.nu) == pytest.approx(1e4)
