@@ -3,7 +3,7 @@
  * lattice Boltzmann method for thermal convection (Schupbach & Premnath, arXiv 2504.09041).
  *
  * One time step advances two coupled lattices at every node: the flow populations f (D2Q9,
- * App. A; or D3Q27, Sec. 4.1-4.3) relaxed toward the FP central-moment attractors with the
+ * App. A; or D3Q27, Sec. 5.1-5.2) relaxed toward the FP central-moment attractors with the
  * renormalized diffusion tensor and the Boussinesq source, and the energy populations g (D2Q9,
  * App. B; or D3Q15, App. C) relaxed toward their own (option-A) attractors.  The step is one fused
  * pull-stream + collide kernel launch (Eqs. LBMsteps-collide / LBMsteps-stream).
@@ -13,7 +13,7 @@
  *    the ABI.  lbm_last_error(h) describes the most recent failure on h (or of lbm_create when
  *    h is NULL).
  *  - Node index i = x + nx * (y + ny * z), x fastest.  Population arrays are [q][nz][ny][nx] in
- *    the paper's link order (D2Q9 Eqs. ex, ey; D3Q27 Sec. 4.2; D3Q15 Sec. 4.4).
+ *    the paper's link order (D2Q9 Eqs. ex, ey; D3Q27 Sec. 5.2; D3Q15 Sec. 5.4).
  *  - Faces are numbered 0..5 = -x, +x, -y, +y, -z, +z.  2D boxes have nz = 1 and ignore the z faces.
  *  - The library owns its device buffers (allocated through lbm_set_allocator's hook, cudaMalloc by
  *    default).  Caller buffers are only read or written during the call that receives them.
@@ -57,14 +57,14 @@ enum lbm_prec {
 enum lbm_face_bc {
     LBM_PERIODIC = 0,        /* both faces of an axis must be periodic, or neither */
     LBM_WALL_ADIABATIC = 1,  /* half-way bounce-back of f (no slip) and of g (zero heat flux) */
-    LBM_WALL_FIXED_T = 2     /* bounce-back of f, anti-bounce-back of g at T_wall (Sec. 5.1) */
+    LBM_WALL_FIXED_T = 2     /* bounce-back of f, anti-bounce-back of g at T_wall (Sec. 6.1) */
 };
 
 typedef struct {
     int face[6];                /* lbm_face_bc of -x, +x, -y, +y, -z, +z */
     double T_wall[6];           /* wall temperature of LBM_WALL_FIXED_T faces */
     double T_init;              /* initial uniform temperature */
-    double T_ref;               /* T_o of the Boussinesq force F = g beta (T - T_o) (Sec. 5.1) */
+    double T_ref;               /* T_o of the Boussinesq force F = g beta (T - T_o) (Sec. 6.1) */
     int gravity_axis;           /* axis of the buoyancy force: 1 (y) in 2D, 2 (z) in 3D */
     unsigned long long seed;    /* splitmix64 seed of the initial temperature perturbation */
     double perturb;             /* T_init += perturb * (2 U_i - 1), U_i uniform in [0, 1) */
@@ -76,7 +76,7 @@ typedef struct {
     double L;                   /* characteristic length: nodes across the fixed-T faces' axis */
     double dT;                  /* T_H - T_C over the fixed-T faces (1 if fewer than two differ) */
     double U, nu, alpha, gbeta; /* U_o = Ma/sqrt(3); nu = U L sqrt(Pr/Ra); alpha = nu/Pr;
-                                   g beta = U^2/(L dT)   (Sec. 5.1, Sec. 6) */
+                                   g beta = U^2/(L dT)   (Sec. 6.1, Sec. 7) */
     double T_ref;
     double om_f[27], om_g[15];  /* relaxation rates in use (see lbm_set_omegas) */
     long long steps;            /* time steps taken since creation */
@@ -97,8 +97,8 @@ LBM_API int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void* ctx
 
 /*
  * Create a box of nx * ny * nz nodes (nz = 1 for LBM_D2Q9_D2Q9) for the cavity problems of
- * Sec. 5.1 / 5.2: Rayleigh number Ra, Prandtl number Pr and Mach number Ma = sqrt(3) U_o
- * (Sec. 6) fix nu, alpha and g beta (see lbm_info_t) and the rates
+ * Sec. 6.1 / 6.2: Rayleigh number Ra, Prandtl number Pr and Mach number Ma = sqrt(3) U_o
+ * (Sec. 7) fix nu, alpha and g beta (see lbm_info_t) and the rates
  *   nu = c_s^2 (1/omega - 1/2)        on the shear moments of f (App. A: omega_4, omega_5),
  *   alpha = c_s^2 (1/omega - 1/2)     on the first-order moments of g (App. B, App. C),
  * every other rate 1.0 (App. A, B, C).  The populations start at the rest attractors at density 1
@@ -120,7 +120,7 @@ LBM_API int lbm_set_stream(lbm_handle h, void* stream);
  *  - D2Q9 f: omega_0..omega_8 of App. A Step 3 (omega_3 on kappa_2s, omega_4 on kappa_2d).
  *  - D2Q9 g: omega_0..omega_8 of App. B Step 3 (omega_3, omega_4 on the eta_2s, eta_2d pair).
  *  - D3Q15 g: omega_0..omega_14 of App. C Step 3.
- *  - D3Q27 f: one rate per entry of the central-moment vector of Sec. 4.2, except slot 7 which
+ *  - D3Q27 f: one rate per entry of the central-moment vector of Sec. 5.2, except slot 7 which
  *    relaxes the trace kappa_200 + kappa_020 + kappa_002 and slots 8, 9 which relax the deviators
  *    kappa_200 - kappa_020 and kappa_200 - kappa_002.
  * Every rate must lie in (0, 2) (App. A).  Errors: LBM_EINVAL.
@@ -140,7 +140,7 @@ LBM_API int lbm_info(lbm_handle h, lbm_info_t* out);
  * Advance n >= 0 time steps (asynchronous on the handle's stream).  Runs of graph_steps steps (32 by
  * default) are replayed from a CUDA graph captured once per buffer parity and launch settings;
  * the rest are plain launches.  Per step one fused launch that
- * pulls the post-collision populations along every link with the wall rules of Sec. 5.1, forms
+ * pulls the post-collision populations along every link with the wall rules of Sec. 6.1, forms
  * T = sum g, F = g beta (T - T_o) along gravity, rho = sum f, rho u = sum f e + F/2 (App. A Step 7),
  * and relaxes f and g in central-moment space (App. A/B/C Steps 1-5).
  * Errors: LBM_EINVAL (n < 0), LBM_ECUDA (launch failure).  Divergence is reported by lbm_sync.
@@ -160,7 +160,7 @@ LBM_API int lbm_fields(lbm_handle h, double* rho, double* ux, double* uy, double
                int device_ptrs);
 
 /*
- * Wall Nusselt number on a fixed-temperature face (Sec. 5.1): at every wall node,
+ * Wall Nusselt number on a fixed-temperature face (Sec. 6.1): at every wall node,
  *   dT/dn = -8/3 T_w + 3 T_1 - 1/3 T_2   (wall at 0, node layers at 1/2 and 3/2, n into the fluid)
  *   Nu = -s (L / dT) dT/dn,  s = +1 if the face's T_wall >= T_ref, else -1,
  * reduced in FP64 to the mean over the face nodes and the max / min with their tangential node
@@ -247,6 +247,76 @@ LBM_API const char* lbm_status_string(int status);
 LBM_API int lbm_nusselt_static(int lattice, int nx, int ny, int nz, const int face_kind[6],
                                const double T_wall[6], double T_ref, const void* g, int face,
                                double L, double dT, double* result, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Batches of 2D boxes.  The paper's studies run many independent cavities that differ in size,
+ * Rayleigh and Prandtl number (Sec. 6.1: Ra = 10^3 .. 10^10 at Pr = 0.71 and grids up to 512^2;
+ * Sec. 7: sweeps of Ma, resolution and Pr = 0.1 .. 5).  A batch holds such members (D2Q9 flow and
+ * energy lattices, one storage precision) and advances all of them by one time step with ONE
+ * persistent kernel launch: the members' populations are concatenated in the same [q][y][x]
+ * layout, the launch's (SM count x CTAs per SM) blocks stride over the list of every member's
+ * tiles, and each member keeps its own geometry, relaxation rates and divergence flag.  Every
+ * member's step is the same arithmetic as lbm_step on a handle created with the same arguments,
+ * so the two give bitwise identical populations.
+ * Batch handles follow the conventions of lbm_handle (allocator hook, stream, not thread-safe).
+ * ------------------------------------------------------------------------------------------- */
+typedef struct lbm_batch_s* lbm_batch;
+
+typedef struct {
+    int count;                      /* members */
+    long long total_nodes;          /* sum of nx * ny over the members */
+    int n_tiles;                    /* tiles of the current tile shape over all members */
+    int tile_x, tile_y;             /* nodes per tile along x and y (one node per thread) */
+    int ctas_per_sm;                /* resident blocks the launch asks for on each SM */
+    int grid;                       /* blocks of one step launch: min(n_tiles, SMs * ctas_per_sm) */
+    int graph_steps;                /* steps per CUDA graph replay (0 = plain launches) */
+    long long steps;                /* time steps taken */
+    double bytes_per_node_update;   /* bytes moved per node and step (18 populations in and out) */
+} lbm_batch_info_t;
+
+/* Create a batch of `count` 2D boxes.  lattice must be LBM_D2Q9_D2Q9 OR-ed with one lbm_prec;
+ * member k has size nx[k] x ny[k], Rayleigh number Ra[k], Prandtl number Pr[k], boundary and
+ * initial conditions bc[k] (as lbm_create), and all members share Ma.  Every member is mapped to
+ * lattice units and initialised exactly as lbm_create maps and initialises a single box.
+ * Errors: LBM_ENOTSUP for a 3D lattice, LBM_EINVAL for an empty batch, a NULL array or a member
+ * that lbm_create would reject (the message names the member), LBM_ENOMEM, LBM_ECUDA.
+ * lbm_batch_last_error(NULL) describes a failed create. */
+LBM_API int lbm_batch_create(int lattice, int count, const int* nx, const int* ny, const double* Ra,
+                             const double* Pr, double Ma, const lbm_bc* bc, lbm_batch* out);
+LBM_API int lbm_batch_destroy(lbm_batch b);
+LBM_API int lbm_batch_set_stream(lbm_batch b, void* stream);
+
+/* Launch shape of the step: tiles of tile_x x tile_y nodes (tile_x in {32, 64, 128, 256},
+ * tile_x * tile_y <= 256 threads), ctas_per_sm blocks per SM (ctas_per_sm * threads <= 2048), and
+ * graph_steps steps per CUDA graph replay (0..4096, rounded up to even; 0 = plain launches).
+ * Default 64 x 2 tiles, 8 CTAs per SM, 32 graph steps.  Errors: LBM_EINVAL for another shape. */
+LBM_API int lbm_batch_set_launch(lbm_batch b, int tile_x, int tile_y, int ctas_per_sm, int graph_steps);
+
+/* Autotuner: time trial_steps steps of every valid (tile shape, CTAs per SM) pair from a fixed
+ * list on a device copy of the current populations, keep the fastest, and report it through the
+ * optional outputs.  The batch's own state and step count are unchanged (divergence flags are
+ * cleared).  Needs device memory for two extra copies of the populations (LBM_ENOMEM otherwise). */
+LBM_API int lbm_batch_tune(lbm_batch b, int trial_steps, int* tile_x, int* tile_y, int* ctas_per_sm);
+
+/* Advance every member by n time steps (n >= 0), on the batch's stream, without waiting. */
+LBM_API int lbm_batch_step(lbm_batch b, long n);
+
+/* Wait for the batch's stream; if diverged is not NULL, diverged[k] = 1 when member k saw a
+ * non-finite or non-positive density or a non-finite temperature (0 otherwise).  Returns
+ * LBM_EDIVERGED if any member did. */
+LBM_API int lbm_batch_sync(lbm_batch b, int* diverged);
+
+/* Wall Nusselt numbers of a fixed-temperature face of one member, as lbm_nusselt. */
+LBM_API int lbm_batch_nusselt(lbm_batch b, int member, int face, double* mean, double* nu_max,
+                              double* nu_min, int* j_max, int* j_min);
+
+/* Populations of one member as FP64 host arrays [9][ny][nx] (f and g), as lbm_get_populations
+ * and lbm_set_populations. */
+LBM_API int lbm_batch_get_populations(lbm_batch b, int member, double* f, double* g);
+LBM_API int lbm_batch_set_populations(lbm_batch b, int member, const double* f, const double* g);
+
+LBM_API int lbm_batch_info(lbm_batch b, lbm_batch_info_t* info);
+LBM_API const char* lbm_batch_last_error(lbm_batch b);
 
 #ifdef __cplusplus
 }

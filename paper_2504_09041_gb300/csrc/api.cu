@@ -129,23 +129,6 @@ size_t pop_bytes(const lbm_s* h)
     return (size_t)(h->qf + h->qg) * (size_t)h->geo.n * lbm::storage_bytes(h->prec);
 }
 
-// Default rates (App. A, B, C): shear / diffusivity rates from nu / alpha, every other rate 1.
-void default_rates(lbm_s* h, double om_nu, double om_alpha, double om_bulk)
-{
-    for (int a = 0; a < 27; ++a) h->hc.om_f[a] = 1.0;
-    for (int b = 0; b < 15; ++b) h->hc.om_g[b] = 1.0;
-    if (h->dim == 2) {
-        h->hc.om_f[3] = om_bulk;
-        h->hc.om_f[4] = h->hc.om_f[5] = om_nu;
-        h->hc.om_g[1] = h->hc.om_g[2] = om_alpha;
-    } else {
-        h->hc.om_f[4] = h->hc.om_f[5] = h->hc.om_f[6] = om_nu;
-        h->hc.om_f[7] = om_bulk;
-        h->hc.om_f[8] = h->hc.om_f[9] = om_nu;
-        h->hc.om_g[1] = h->hc.om_g[2] = h->hc.om_g[3] = om_alpha;
-    }
-}
-
 // Device temporary of n doubles for host <-> device staging.
 struct Tmp {
     lbm_s* h;
@@ -191,52 +174,65 @@ const char* lbm_last_error(lbm_handle h)
     return h ? h->err.c_str() : g_create_error.c_str();
 }
 
-int lbm_create(int lattice, int nx, int ny, int nz, double Ra, double Pr, double Ma,
-               const lbm_bc* bc, lbm_handle* out)
+}  // extern "C"
+
+namespace lbm {
+
+void current_allocator(lbm_alloc_fn* a, lbm_free_fn* f, void** ctx)
 {
-    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
-    *out = nullptr;
+    *a = g_alloc;
+    *f = g_free;
+    *ctx = g_ctx;
+}
+
+// Validate a box description and derive its parameters (Sec. 6.1, Sec. 7): L across the fixed-T
+// faces, U = Ma / sqrt(3), g beta dT L = U^2, nu = U L sqrt(Pr / Ra), alpha = nu / Pr, and the
+// rates of App. A/B/C.  On failure returns the status and sets *err.
+int plan_box(int lattice, int nx, int ny, int nz, double Ra, double Pr, double Ma, const lbm_bc* bc,
+             BoxPlan* P, std::string* err)
+{
+    char buf[256];
+    auto bad = [&](int code, const char* fmt, auto... a) {
+        snprintf(buf, sizeof buf, fmt, a...);
+        *err = buf;
+        return code;
+    };
     const int lat = lattice & 0xff;
     const int prec_code = lattice & ~0xff;
-    if (lat != LBM_D2Q9_D2Q9 && lat != LBM_D3Q27_D3Q15)
-        return fail(nullptr, LBM_EINVAL, "unknown lattice %d", lat);
+    if (lat != LBM_D2Q9_D2Q9 && lat != LBM_D3Q27_D3Q15) return bad(LBM_EINVAL, "unknown lattice %d", lat);
     int prec;
-    if (prec_code == LBM_FP64) prec = lbm::kF64;
-    else if (prec_code == LBM_FP32) prec = lbm::kF32;
-    else if (prec_code == LBM_FP16S) prec = lbm::kF16S;
-    else return fail(nullptr, LBM_EINVAL, "unknown precision flag 0x%x", prec_code);
+    if (prec_code == LBM_FP64) prec = kF64;
+    else if (prec_code == LBM_FP32) prec = kF32;
+    else if (prec_code == LBM_FP16S) prec = kF16S;
+    else return bad(LBM_EINVAL, "unknown precision flag 0x%x", prec_code);
     const int dim = lat == LBM_D2Q9_D2Q9 ? 2 : 3;
     if (dim == 2 && nz == 0) nz = 1;
-    if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "box %d x %d x %d is empty", nx, ny, nz);
-    if (dim == 2 && nz != 1) return fail(nullptr, LBM_EINVAL, "2D boxes need nz = 1");
-    if ((long long)nx * ny * nz > INT_MAX) return fail(nullptr, LBM_EINVAL, "more than 2^31 - 1 nodes");
-    if (nz > 65535 || (ny + 1) / 2 > 65535) return fail(nullptr, LBM_EINVAL, "box too tall for the launch grid");
+    if (nx < 1 || ny < 1 || nz < 1) return bad(LBM_EINVAL, "box %d x %d x %d is empty", nx, ny, nz);
+    if (dim == 2 && nz != 1) return bad(LBM_EINVAL, "2D boxes need nz = 1");
+    if ((long long)nx * ny * nz > INT_MAX) return bad(LBM_EINVAL, "more than 2^31 - 1 nodes");
+    if (nz > 65535 || (ny + 1) / 2 > 65535) return bad(LBM_EINVAL, "box too tall for the launch grid");
     if (!(std::isfinite(Ra) && Ra > 0) || !(std::isfinite(Pr) && Pr > 0) || !(std::isfinite(Ma) && Ma > 0))
-        return fail(nullptr, LBM_EINVAL, "Ra, Pr and Ma must be positive and finite");
-    if (!bc) return fail(nullptr, LBM_EINVAL, "bc is NULL");
+        return bad(LBM_EINVAL, "Ra, Pr and Ma must be positive and finite");
+    if (!bc) return bad(LBM_EINVAL, "bc is NULL");
     for (int f = 0; f < 6; ++f)
         if (bc->face[f] < LBM_PERIODIC || bc->face[f] > LBM_WALL_FIXED_T)
-            return fail(nullptr, LBM_EINVAL, "face %d: unknown kind %d", f, bc->face[f]);
+            return bad(LBM_EINVAL, "face %d: unknown kind %d", f, bc->face[f]);
     for (int ax = 0; ax < dim; ++ax)
         if ((bc->face[2 * ax] == LBM_PERIODIC) != (bc->face[2 * ax + 1] == LBM_PERIODIC))
-            return fail(nullptr, LBM_EINVAL, "axis %d is periodic on one face only", ax);
+            return bad(LBM_EINVAL, "axis %d is periodic on one face only", ax);
     if (bc->gravity_axis < 0 || bc->gravity_axis >= dim)
-        return fail(nullptr, LBM_EINVAL, "gravity axis %d out of range", bc->gravity_axis);
+        return bad(LBM_EINVAL, "gravity axis %d out of range", bc->gravity_axis);
 
-    lbm_s* h = new lbm_s;
-    h->alloc = g_alloc;
-    h->dealloc = g_free;
-    h->actx = g_ctx;
-    h->lattice = lat;
-    h->prec = prec;
-    h->dim = dim;
-    h->nx = nx;
-    h->ny = ny;
-    h->nz = nz;
-    h->qf = dim == 2 ? 9 : 27;
-    h->qg = dim == 2 ? 9 : 15;
-    h->bc = *bc;
-    lbm::Geometry& g = h->geo;
+    P->lattice = lat;
+    P->prec = prec;
+    P->dim = dim;
+    P->nx = nx;
+    P->ny = ny;
+    P->nz = nz;
+    P->qf = dim == 2 ? 9 : 27;
+    P->qg = dim == 2 ? 9 : 15;
+    Geometry& g = P->geo;
+    g = Geometry{};
     g.nx = nx;
     g.ny = ny;
     g.nz = nz;
@@ -247,31 +243,82 @@ int lbm_create(int lattice, int nx, int ny, int nz, double Ra, double Pr, double
         g.T_wall[f] = bc->T_wall[f];
         g.profile[f] = nullptr;
     }
-
-    // Problem parameters (Sec. 5.1, Sec. 6): L across the fixed-T faces, U = Ma / sqrt(3),
-    // g beta dT L = U^2, nu = U L sqrt(Pr / Ra), alpha = nu / Pr.
     const int ext[3] = {nx, ny, nz};
-    h->L = nx;
+    P->L = nx;
     double tmin = INFINITY, tmax = -INFINITY;
     int nfixed = 0;
     for (int f = 2 * dim - 1; f >= 0; --f)
-        if (g.kind[f] == LBM_WALL_FIXED_T) h->L = ext[f / 2];
+        if (g.kind[f] == LBM_WALL_FIXED_T) P->L = ext[f / 2];
     for (int f = 0; f < 2 * dim; ++f)
         if (g.kind[f] == LBM_WALL_FIXED_T) {
             ++nfixed;
             tmin = fmin(tmin, bc->T_wall[f]);
             tmax = fmax(tmax, bc->T_wall[f]);
         }
-    h->dT = (nfixed >= 2 && tmax > tmin) ? tmax - tmin : 1.0;
-    h->U = Ma / std::sqrt(3.0);
-    h->nu = h->U * h->L * std::sqrt(Pr / Ra);
-    h->alpha = h->nu / Pr;
-    h->hc.gbeta = h->U * h->U / (h->L * h->dT);
-    h->hc.T_ref = bc->T_ref;
-    h->hc.gaxis = bc->gravity_axis;
-    const double om_nu = 1.0 / (3.0 * h->nu + 0.5);
-    const double om_alpha = 1.0 / (3.0 * h->alpha + 0.5);
-    default_rates(h, om_nu, om_alpha, 1.0);
+    P->dT = (nfixed >= 2 && tmax > tmin) ? tmax - tmin : 1.0;
+    P->U = Ma / std::sqrt(3.0);
+    P->nu = P->U * P->L * std::sqrt(Pr / Ra);
+    P->alpha = P->nu / Pr;
+    HostCoeffs& hc = P->hc;
+    hc = HostCoeffs{};
+    hc.gbeta = P->U * P->U / (P->L * P->dT);
+    hc.T_ref = bc->T_ref;
+    hc.gaxis = bc->gravity_axis;
+    const double om_nu = 1.0 / (3.0 * P->nu + 0.5);
+    const double om_alpha = 1.0 / (3.0 * P->alpha + 0.5);
+    // App. A, B, C: shear / diffusivity rates from nu / alpha, bulk and every free rate 1
+    for (int a = 0; a < 27; ++a) hc.om_f[a] = 1.0;
+    for (int b = 0; b < 15; ++b) hc.om_g[b] = 1.0;
+    if (dim == 2) {
+        hc.om_f[4] = hc.om_f[5] = om_nu;
+        hc.om_g[1] = hc.om_g[2] = om_alpha;
+    } else {
+        hc.om_f[4] = hc.om_f[5] = hc.om_f[6] = om_nu;
+        hc.om_f[8] = hc.om_f[9] = om_nu;
+        hc.om_g[1] = hc.om_g[2] = hc.om_g[3] = om_alpha;
+    }
+    return LBM_OK;
+}
+
+}  // namespace lbm
+
+extern "C" {
+
+int lbm_create(int lattice, int nx, int ny, int nz, double Ra, double Pr, double Ma,
+               const lbm_bc* bc, lbm_handle* out)
+{
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    lbm::BoxPlan P;
+    std::string err;
+    const int rc = lbm::plan_box(lattice, nx, ny, nz, Ra, Pr, Ma, bc, &P, &err);
+    if (rc) return fail(nullptr, rc, "%s", err.c_str());
+    const int prec = P.prec, dim = P.dim;
+    nx = P.nx;
+    ny = P.ny;
+    nz = P.nz;
+
+    lbm_s* h = new lbm_s;
+    h->alloc = g_alloc;
+    h->dealloc = g_free;
+    h->actx = g_ctx;
+    h->lattice = P.lattice;
+    h->prec = prec;
+    h->dim = dim;
+    h->nx = nx;
+    h->ny = ny;
+    h->nz = nz;
+    h->qf = P.qf;
+    h->qg = P.qg;
+    h->bc = *bc;
+    h->geo = P.geo;
+    lbm::Geometry& g = h->geo;
+    h->L = P.L;
+    h->dT = P.dT;
+    h->U = P.U;
+    h->nu = P.nu;
+    h->alpha = P.alpha;
+    h->hc = P.hc;
 
     // Device memory.
     const size_t sb = lbm::storage_bytes(prec);

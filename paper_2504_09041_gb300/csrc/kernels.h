@@ -5,6 +5,8 @@
 #include <cstdint>
 
 #include "lbm_common.cuh"
+#include "../../include/lbm.h"
+#include <string>
 
 namespace lbm {
 
@@ -19,6 +21,18 @@ struct HostCoeffs {
 };
 
 size_t storage_bytes(int prec);
+
+// A validated box and its derived parameters (plan_box in api.cu).
+struct BoxPlan {
+    int lattice, prec, dim, nx, ny, nz, qf, qg;
+    Geometry geo;
+    HostCoeffs hc;
+    double L, dT, U, nu, alpha;
+};
+int plan_box(int lattice, int nx, int ny, int nz, double Ra, double Pr, double Ma, const lbm_bc* bc,
+             BoxPlan* P, std::string* err);
+// The process-wide device allocator hooks of lbm_set_allocator.
+void current_allocator(lbm_alloc_fn* a, lbm_free_fn* f, void** ctx);
 
 // block: thread-block shape of the step launch (x-major); block.x == 0 selects the default.
 cudaError_t launch_step(int dim, int prec, const void* fin, const void* gin, void* fout, void* gout,

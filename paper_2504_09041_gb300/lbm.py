@@ -51,6 +51,14 @@ class lbm_info_t(ctypes.Structure):
                 ("graph_steps", ctypes.c_int)]
 
 
+class lbm_batch_info_t(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("total_nodes", ctypes.c_longlong),
+                ("n_tiles", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int), ("grid", ctypes.c_int),
+                ("graph_steps", ctypes.c_int), ("steps", ctypes.c_longlong),
+                ("bytes_per_node_update", ctypes.c_double)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -88,6 +96,17 @@ def lib() -> ctypes.CDLL:
             "lbm_set_state": [H, v, s],
             "lbm_nusselt_static": [i, i, i, i, ip, dp, d, v, i, d, d, v, v],
             "lbm_adjoint_step": [H, ctypes.c_long, i, i, dp, dp, ctypes.c_long],
+            "lbm_batch_create": [i, i, ip, ip, dp, dp, d, ctypes.POINTER(lbm_bc), ctypes.POINTER(H)],
+            "lbm_batch_destroy": [H],
+            "lbm_batch_set_stream": [H, v],
+            "lbm_batch_set_launch": [H, i, i, i, i],
+            "lbm_batch_tune": [H, i, ip, ip, ip],
+            "lbm_batch_step": [H, ctypes.c_long],
+            "lbm_batch_sync": [H, ip],
+            "lbm_batch_nusselt": [H, i, i, dp, dp, dp, ip, ip],
+            "lbm_batch_get_populations": [H, i, dp, dp],
+            "lbm_batch_set_populations": [H, i, dp, dp],
+            "lbm_batch_info": [H, ctypes.POINTER(lbm_batch_info_t)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -95,6 +114,8 @@ def lib() -> ctypes.CDLL:
             fn.restype = ctypes.c_int
         L.lbm_last_error.argtypes = [H]
         L.lbm_last_error.restype = ctypes.c_char_p
+        L.lbm_batch_last_error.argtypes = [H]
+        L.lbm_batch_last_error.restype = ctypes.c_char_p
         L.lbm_status_string.argtypes = [i]
         L.lbm_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -227,6 +248,82 @@ def lbm_nusselt_static(lattice: int, nx: int, ny: int, nz: int, face_kind, T_wal
         why = (f"face {face} has {n_face} nodes, more than {NUSSELT_STATIC_MAX_FACE_NODES}"
                if n_face > NUSSELT_STATIC_MAX_FACE_NODES else "invalid arguments or CUDA failure")
         raise LbmError(st, f"lbm_nusselt_static: {why}")
+
+
+def _bcheck(status: int, b=None):
+    if status != LBM_OK:
+        msg = lib().lbm_batch_last_error(b).decode()
+        raise LbmError(status, msg or lib().lbm_status_string(status).decode())
+
+
+def lbm_batch_create(lattice: int, nx, ny, Ra, Pr, Ma: float, bcs) -> ctypes.c_void_p:
+    n = len(nx)
+    if not (len(ny) == len(Ra) == len(Pr) == len(bcs) == n):
+        raise ValueError("nx, ny, Ra, Pr and bcs must have one entry per member")
+    b = ctypes.c_void_p()
+    _bcheck(lib().lbm_batch_create(lattice, n, (ctypes.c_int * n)(*nx), (ctypes.c_int * n)(*ny),
+                                   (ctypes.c_double * n)(*Ra), (ctypes.c_double * n)(*Pr), Ma,
+                                   (lbm_bc * n)(*bcs), ctypes.byref(b)))
+    return b
+
+
+def lbm_batch_destroy(b):
+    _bcheck(lib().lbm_batch_destroy(b), b)
+
+
+def lbm_batch_set_stream(b, stream: int):
+    _bcheck(lib().lbm_batch_set_stream(b, ctypes.c_void_p(stream)), b)
+
+
+def lbm_batch_set_launch(b, tile_x: int, tile_y: int, ctas_per_sm: int, graph_steps: int):
+    _bcheck(lib().lbm_batch_set_launch(b, tile_x, tile_y, ctas_per_sm, graph_steps), b)
+
+
+def lbm_batch_tune(b, trial_steps: int):
+    """Autotune the launch shape; returns (tile_x, tile_y, ctas_per_sm)."""
+    tx, ty, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _bcheck(lib().lbm_batch_tune(b, trial_steps, ctypes.byref(tx), ctypes.byref(ty),
+                                 ctypes.byref(c)), b)
+    return tx.value, ty.value, c.value
+
+
+def lbm_batch_step(b, n: int):
+    _bcheck(lib().lbm_batch_step(b, n), b)
+
+
+def lbm_batch_sync(b, count: int):
+    """Per-member divergence flags (numpy int32); raises nothing for diverged members."""
+    flags = np.zeros(count, dtype=np.int32)
+    st = lib().lbm_batch_sync(b, flags.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if st not in (LBM_OK, LBM_EDIVERGED):
+        _bcheck(st, b)
+    return flags
+
+
+def lbm_batch_nusselt(b, member: int, face: int):
+    mean, mx, mn = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    jx, jn = ctypes.c_int(), ctypes.c_int()
+    _bcheck(lib().lbm_batch_nusselt(b, member, face, ctypes.byref(mean), ctypes.byref(mx),
+                                    ctypes.byref(mn), ctypes.byref(jx), ctypes.byref(jn)), b)
+    return mean.value, mx.value, mn.value, jx.value, jn.value
+
+
+def lbm_batch_get_populations(b, member: int, f: np.ndarray, g: np.ndarray):
+    _bcheck(lib().lbm_batch_get_populations(b, member, _dptr(f.ctypes.data), _dptr(g.ctypes.data)), b)
+
+
+def lbm_batch_set_populations(b, member: int, f: np.ndarray, g: np.ndarray):
+    _bcheck(lib().lbm_batch_set_populations(b, member, _dptr(f.ctypes.data), _dptr(g.ctypes.data)), b)
+
+
+def lbm_batch_info(b) -> lbm_batch_info_t:
+    out = lbm_batch_info_t()
+    _bcheck(lib().lbm_batch_info(b, ctypes.byref(out)), b)
+    return out
+
+
+def lbm_batch_last_error(b=None) -> str:
+    return lib().lbm_batch_last_error(b).decode()
 
 
 def lbm_last_error(h=None) -> str:
@@ -410,6 +507,73 @@ class Lattice:
 
     def set_state(self, buf: np.ndarray):
         lbm_set_state(self.h, np.ascontiguousarray(buf, dtype=np.uint8))
+
+
+class Batch:
+    """Many 2D boxes advanced together by one persistent launch per step (lbm_batch_*)."""
+
+    def __init__(self, sizes, Ra, Pr, Ma: float = 0.1, walls=None, precision: str = "fp32",
+                 stream=None, torch_allocator: bool = True):
+        import torch
+        self.torch = torch
+        if torch_allocator:
+            use_torch_allocator()
+        else:
+            use_cuda_allocator()
+        self.sizes = [(int(a), int(b)) for a, b in sizes]
+        self.count = len(self.sizes)
+        if walls is None:
+            walls = [Walls.cavity(2)] * self.count
+        elif isinstance(walls, Walls):
+            walls = [walls] * self.count
+        self.walls = list(walls)
+        self.b = lbm_batch_create(LBM_D2Q9_D2Q9 | PRECISIONS[precision],
+                                  [s[0] for s in self.sizes], [s[1] for s in self.sizes],
+                                  list(Ra), list(Pr), Ma, [w.to_c() for w in self.walls])
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        lbm_batch_set_stream(self.b, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> lbm_batch_info_t:
+        return lbm_batch_info(self.b)
+
+    def set_launch(self, tile_x: int, tile_y: int, ctas_per_sm: int, graph_steps: int = 32):
+        lbm_batch_set_launch(self.b, tile_x, tile_y, ctas_per_sm, graph_steps)
+
+    def tune(self, trial_steps: int = 20):
+        return lbm_batch_tune(self.b, trial_steps)
+
+    def step(self, n: int = 1):
+        lbm_batch_step(self.b, n)
+
+    def sync(self):
+        """Wait for the batch; returns the per-member divergence flags."""
+        return lbm_batch_sync(self.b, self.count)
+
+    def nusselt(self, member: int, face: int):
+        return lbm_batch_nusselt(self.b, member, face)
+
+    def get_populations(self, member: int):
+        nx, ny = self.sizes[member]
+        f = np.empty((9, 1, ny, nx)); g = np.empty((9, 1, ny, nx))
+        lbm_batch_get_populations(self.b, member, f, g)
+        return f, g
+
+    def set_populations(self, member: int, f, g):
+        nx, ny = self.sizes[member]
+        f = np.ascontiguousarray(f, dtype=np.float64); g = np.ascontiguousarray(g, dtype=np.float64)
+        assert f.size == 9 * nx * ny and g.size == 9 * nx * ny
+        lbm_batch_set_populations(self.b, member, f, g)
 
 
 def wall_nusselt_objective(lattice: "Lattice", state0, n_steps: int, objective_face: int,

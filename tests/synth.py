@@ -3,9 +3,10 @@
 This module holds no arithmetic of the method: it only draws reproducible random numbers and
 scales given arrays with them.
 """
-import math
 
 import numpy as np
+
+from paper_2504_09041_gb300.workloads import ensemble_2d, sine_profile  # noqa: F401 (shared draws)
 
 
 def perturbed(base: np.ndarray, seed: int, scale: float) -> np.ndarray:
@@ -19,11 +20,6 @@ def rates(seed: int, n: int, lo: float = 0.6, hi: float = 1.9) -> np.ndarray:
     return np.random.default_rng(seed).uniform(lo, hi, n)
 
 
-def sine_profile(seed: int, n: int, base: float = 1.0, amp: float = 0.05, modes: int = 4):
-    """base + amp * sum_k a_k sin(pi k (j + 1/2) / n), a_k uniform in [-1, 1], j = 0..n-1."""
-    a = np.random.default_rng(seed).uniform(-1.0, 1.0, modes)
-    j = np.arange(n) + 0.5
-    return base + amp * sum(a[k] * np.sin(math.pi * (k + 1) * j / n) for k in range(modes))
 
 
 def sample_nodes(seed: int, shape, count: int, include_corners: bool = True):

@@ -97,3 +97,34 @@ def test_binding_fails_loudly_without_the_library(lbm, monkeypatch):
     monkeypatch.setattr(lbm, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "liblbm.so"))
     with pytest.raises(ImportError):
         lbm.lib()
+
+
+def test_batch_create_rejects_bad_requests(lbm):
+    cav = lbm.Walls.cavity(2).to_c()
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_batch_create(lbm.LBM_D3Q27_D3Q15 | lbm.LBM_FP32, [8], [8], [1e4], [0.71], 0.1,
+                             [lbm.Walls.cavity(3).to_c()])
+    assert e.value.status == lbm.LBM_ENOTSUP
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_batch_create(lbm.LBM_D2Q9_D2Q9 | lbm.LBM_FP32, [8, 0], [8, 8], [1e4, 1e4],
+                             [0.71, 0.71], 0.1, [cav, cav])
+    assert e.value.status == lbm.LBM_EINVAL and "member 1" in str(e.value)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_batch_create(lbm.LBM_D2Q9_D2Q9 | lbm.LBM_FP32, [8, 8], [8, 8], [1e4, -1.0],
+                             [0.71, 0.71], 0.1, [cav, cav])
+    assert e.value.status == lbm.LBM_EINVAL and "member 1" in str(e.value)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_batch_create(lbm.LBM_D2Q9_D2Q9 | lbm.LBM_FP32, [], [], [], [], 0.1, [])
+    assert e.value.status == lbm.LBM_EINVAL
+    with pytest.raises(ValueError):
+        lbm.lbm_batch_create(lbm.LBM_D2Q9_D2Q9, [8], [8, 8], [1e4], [0.71], 0.1, [cav])
+
+
+def test_batch_calls_reject_a_null_batch(lbm):
+    L = lbm.lib()
+    assert L.lbm_batch_step(None, 1) == lbm.LBM_EINVAL
+    assert L.lbm_batch_sync(None, None) == lbm.LBM_EINVAL
+    assert L.lbm_batch_destroy(None) == lbm.LBM_EINVAL
+    assert L.lbm_batch_set_launch(None, 64, 2, 8, 32) == lbm.LBM_EINVAL
+    assert L.lbm_batch_info(None, None) == lbm.LBM_EINVAL
+    assert "NULL" in lbm.lbm_batch_last_error(None)
