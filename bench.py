@@ -303,13 +303,15 @@ def measure_forms(L, torch, stream, args):
     """MLUPS and HBM fraction of the other lattice / precision forms on the same GPU."""
     out = []
     peak, _ = hbm_peak()
-    cases = [("d3q27", 256, 256, 256, "fp64", L.Walls.cavity(3), 1e6, 20),
-             ("d3q27", 256, 256, 256, "fp16s", L.Walls.cavity(3), 1e6, 50),
-             ("d2q9", 1024, 512, 1, "fp64", L.Walls.rayleigh_benard(seed=1), 1e8, 200),
-             ("d2q9", 1024, 512, 1, "fp32", L.Walls.rayleigh_benard(seed=1), 1e8, 400),
-             ("d2q9", 1024, 512, 1, "fp16s", L.Walls.rayleigh_benard(seed=1), 1e8, 400)]
-    for lat_name, nx, ny, nz, prec, walls, Ra, k in cases:
+    cases = [("d3q27", 256, 256, 256, "fp64", L.Walls.cavity(3), 1e6, 20, 0),
+             ("d3q27", 256, 256, 256, "fp16s", L.Walls.cavity(3), 1e6, 50, 0),
+             ("d3q27", 256, 256, 256, "fp32", L.Walls.cavity(3), 1e6, 50, 1),
+             ("d2q9", 1024, 512, 1, "fp64", L.Walls.rayleigh_benard(seed=1), 1e8, 200, 0),
+             ("d2q9", 1024, 512, 1, "fp32", L.Walls.rayleigh_benard(seed=1), 1e8, 400, 0),
+             ("d2q9", 1024, 512, 1, "fp16s", L.Walls.rayleigh_benard(seed=1), 1e8, 400, 0)]
+    for lat_name, nx, ny, nz, prec, walls, Ra, k, gopt in cases:
         lat = L.Lattice(lat_name, nx, ny, nz, Ra, 0.71, 0.1, walls=walls, precision=prec, stream=stream)
+        lat.set_param("g_attractors", gopt)
         lat.step(5)
         lat.sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -324,12 +326,14 @@ def measure_forms(L, torch, stream, args):
         out.append({"lattice": "D3Q27+D3Q15" if lat_name == "d3q27" else "D2Q9+D2Q9",
                     "precision": prec, "box": [nx, ny, nz], "mlups": round(lat.n / s / 1e6, 1),
                     "ms_per_step": round(s * 1e3, 4), "gbs": round(gbs, 1),
-                    "hbm_frac": round(gbs / peak, 4), "steps": k})
+                    "hbm_frac": round(gbs / peak, 4), "steps": k,
+                    "g_attractors": "option B" if gopt else "option A"})
         lat.close()
     return out
 
 
-def measure_batched(L, torch, stream, steps: int = 2000, unbatched_steps: int = 256):
+def measure_batched(L, torch, stream, steps: int = 2000, unbatched_steps: int = 256,
+                    compare: bool = True):
     """The ensemble workload: 64 independent square cavities (sides 64..512, Ra log-uniform in
     [1e3, 1e7], Pr uniform in [0.71, 7], seeded), FP32, one autotuned persistent launch per
     step replayed from CUDA graphs.  Compared with the same members advanced one handle at a
@@ -354,6 +358,13 @@ def measure_batched(L, torch, stream, steps: int = 2000, unbatched_steps: int = 
     inf = b.info()
     nodes = inf.total_nodes
     bpn = inf.bytes_per_node_update
+
+    if not compare:
+        b.close()
+        gbs = bpn * nodes / t / 1e9
+        return {"nodes": nodes, "mlups": round(nodes / t / 1e6, 1), "gbs": round(gbs, 1),
+                "hbm_frac": round(gbs / peak, 4), "steps": steps,
+                "launch": {"tile": [tx, ty], "ctas_per_sm": cps, "grid": inf.grid}}
 
     # the same members, one handle each, stepped one after the other on the same stream
     lats = [L.Lattice("d2q9", nx, ny, 1, Ra=Ra[k], Pr=Pr[k], Ma=0.1, precision="fp32",
@@ -399,6 +410,16 @@ def measure_batched(L, torch, stream, steps: int = 2000, unbatched_steps: int = 
             "diverged_members": int(flags.sum()),
             "nusselt_vs_fp64": nu_err,
             "nusselt_max_rel": max(e["rel"] for e in nu_err) if nu_err else None}
+
+
+def run_only(args):
+    """One secondary measurement on its own (used to profile its kernel)."""
+    import torch
+    from paper_2504_09041_gb300 import lbm as L
+    stream = torch.cuda.Stream()
+    if args.only == "batched":
+        return measure_batched(L, torch, stream, steps=args.steps, compare=False)
+    return measure_adjoint(L, torch, stream)
 
 
 def measure_adjoint(L, torch, stream):
@@ -525,12 +546,17 @@ def main(argv=None):
     ap.add_argument("--nx", type=int, default=None, help="override the box (profiling cases)")
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)
+    ap.add_argument("--only", default=None, choices=["batched", "adjoint"],
+                    help="run one secondary measurement alone and print its record (profiling)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     for k in ("nx", "ny", "nz", "precision"):
         if getattr(args, k) is not None:
             WORKLOAD[k] = getattr(args, k)
+    if args.only:
+        print(json.dumps(run_only(args)), flush=True)
+        return
     line = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if line is not None:
         print(json.dumps(line), flush=True)

@@ -84,6 +84,7 @@ typedef struct {
     size_t state_bytes;         /* size of an lbm_get_state checkpoint */
     int block_x, block_y;       /* thread-block shape of the step launch */
     int graph_steps;            /* steps per CUDA graph replayed by lbm_step (0: plain launches) */
+    int g_attractors;           /* energy attractors of orders 3-4: 0 = option A, 1 = option B */
 } lbm_info_t;
 
 /*
@@ -128,7 +129,10 @@ LBM_API int lbm_set_stream(lbm_handle h, void* stream);
 LBM_API int lbm_set_omegas(lbm_handle h, const double* om_f, int n_f, const double* om_g, int n_g);
 
 /* Set a scalar parameter: "gbeta", "T_ref", "omega_nu", "omega_alpha", "omega_bulk",
- * "adjoint_fp64" (0 or 1: arithmetic of lbm_adjoint_step's vector-Jacobian products),
+ * "g_attractors" (0: option A, Eqs. MvT2D / g-attractorsD3Q15optionA, the default and the paper's
+ * choice; 1: option B, the renormalized energy attractors of orders 3-4 of Eq. MvT2DoptionB and
+ * its D3Q15 counterpart in Sec. 5.3, with D-hat' = eta~ / T from the post-collision second
+ * moments), "adjoint_fp64" (0 or 1: arithmetic of lbm_adjoint_step's vector-Jacobian products),
  * "graph_steps" (even count of steps that lbm_step replays as one CUDA graph; 0 disables), or the
  * thread-block shape of the step launch, "block_x" (32, 64, 128 or 256) and "block_y"
  * (block_x * block_y <= 256).  Errors: LBM_EINVAL for an unknown key, a rate outside (0, 2) or a

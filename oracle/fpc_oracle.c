@@ -227,12 +227,15 @@ void orc_d2q9_f_collide(const double f[9], double rho, double ux, double uy, dou
 }
 
 /*
- * Appendix B, Steps 1-5: collision of the energy populations with option-A attractors
- * (Eq. MvT2D).  om[0..8] are the paper's omega_0..omega_8 (omega_1 = omega_2 set by alpha).
- * The second-order pair is relaxed as eta_2s = eta_20 + eta_02 and eta_2d = eta_20 - eta_02
- * with omega_3, omega_4 and then split back, as in Appendix A.
+ * Appendix B, Steps 1-5: collision of the energy populations.  om[0..8] are the paper's
+ * omega_0..omega_8 (omega_1 = omega_2 set by alpha).  The second-order pair is relaxed as
+ * eta_2s = eta_20 + eta_02 and eta_2d = eta_20 - eta_02 with omega_3, omega_4 and then split
+ * back, as in Appendix A.  option 0 takes the option-A attractors of orders 3-4 (Eq. MvT2D),
+ * option 1 the renormalized option-B attractors (Eq. MvT2DoptionB), both from the
+ * post-collision lower moments.
  */
-void orc_d2q9_g_collide(const double g[9], double ux, double uy, const double om[9], double gt[9])
+void orc_d2q9_g_collide(const double g[9], double ux, double uy, const double om[9], int option,
+                        double gt[9])
 {
     double r[9], n[9], nt[9], rt[9];
     orc_d2q9_step1(g, r);
@@ -252,9 +255,16 @@ void orc_d2q9_g_collide(const double g[9], double ux, double uy, const double om
     nt[3] = 0.5 * (nt2s + nt2d);
     nt[4] = 0.5 * (nt2s - nt2d);
 
-    const double Mv21 = (2.0 / 3.0) * CHS2 * nt[2];
-    const double Mv12 = (2.0 / 3.0) * CHS2 * nt[1];
-    const double Mv22 = 0.5 * CHS2 * (nt[3] + nt[4]);
+    double Mv21, Mv12, Mv22;
+    if (option == 0) {
+        Mv21 = (2.0 / 3.0) * CHS2 * nt[2];
+        Mv12 = (2.0 / 3.0) * CHS2 * nt[1];
+        Mv22 = 0.5 * CHS2 * (nt[3] + nt[4]);
+    } else {
+        Mv21 = 2.0 / (3.0 * T) * (nt[3] * nt[2] + 2.0 * nt[5] * nt[1]);
+        Mv12 = 2.0 / (3.0 * T) * (nt[4] * nt[1] + 2.0 * nt[5] * nt[2]);
+        Mv22 = (nt[3] * nt[4] + 2.0 * nt[5] * nt[5]) / T;
+    }
     nt[6] = n[6] + om[6] * (Mv21 - n[6]);
     nt[7] = n[7] + om[7] * (Mv12 - n[7]);
     nt[8] = n[8] + om[8] * (Mv22 - n[8]);
@@ -357,11 +367,13 @@ void orc_d3q15_step5(const double r[15], double g[15])
 }
 
 /*
- * Appendix C, Steps 1-5: D3Q15 energy collision with option-A attractors
- * (Eq. g-attractorsD3Q15optionA, reading R3).  om[0..14] are the paper's omega_0..omega_14.
+ * Appendix C, Steps 1-5: D3Q15 energy collision.  om[0..14] are the paper's omega_0..omega_14.
+ * option 0 takes the option-A attractors of orders 3-4 (Eq. g-attractorsD3Q15optionA, reading
+ * R3), option 1 the renormalized option-B list that follows it in Sec. 5.3, both from the
+ * post-collision moments of orders 0-2.
  */
 void orc_d3q15_g_collide(const double g[15], double ux, double uy, double uz, const double om[15],
-                         double gt[15])
+                         int option, double gt[15])
 {
     double r[15], n[15], nt[15], rt[15];
     orc_d3q15_step1(g, r);
@@ -381,11 +393,22 @@ void orc_d3q15_g_collide(const double g[15], double ux, double uy, double uz, co
     Mv[9] = CHS2 * T;
     for (int j = 0; j <= 9; ++j) nt[j] = n[j] + om[j] * (Mv[j] - n[j]);
 
-    Mv[10] = (2.0 / 3.0) * CHS2 * nt[1];
-    Mv[11] = (2.0 / 3.0) * CHS2 * nt[2];
-    Mv[12] = (2.0 / 3.0) * CHS2 * nt[3];
-    Mv[13] = 0.0;
-    Mv[14] = 0.5 * CHS2 * (nt[7] + nt[8]);
+    if (option == 0) {
+        Mv[10] = (2.0 / 3.0) * CHS2 * nt[1];
+        Mv[11] = (2.0 / 3.0) * CHS2 * nt[2];
+        Mv[12] = (2.0 / 3.0) * CHS2 * nt[3];
+        Mv[13] = 0.0;
+        Mv[14] = 0.5 * CHS2 * (nt[7] + nt[8]);
+    } else {
+        /* moment slots: 1 = 100, 2 = 010, 3 = 001, 4 = 110, 5 = 101, 6 = 011, 7 = 200,
+         * 8 = 020, 9 = 002 */
+        const double c = 2.0 / (3.0 * T);
+        Mv[10] = c * (nt[8] * nt[1] + 2.0 * nt[4] * nt[2]);                  /* 120 */
+        Mv[11] = c * (nt[9] * nt[2] + 2.0 * nt[6] * nt[3]);                  /* 012 */
+        Mv[12] = c * (nt[7] * nt[3] + 2.0 * nt[5] * nt[1]);                  /* 201 */
+        Mv[13] = c * (nt[4] * nt[3] + nt[6] * nt[1] + nt[5] * nt[2]);        /* 111 */
+        Mv[14] = (nt[7] * nt[8] + 2.0 * nt[4] * nt[4]) / T;                  /* 220 */
+    }
     for (int j = 10; j <= 14; ++j) nt[j] = n[j] + om[j] * (Mv[j] - n[j]);
 
     orc_d3q15_step4(nt, ux, uy, uz, rt);
@@ -652,6 +675,7 @@ typedef struct {
     double gbeta, T_ref;
     int gravity_axis;
     double om_f[27], om_g[15];
+    int g_option;              /* energy attractors of orders 3-4: 0 = option A, 1 = option B */
     double wg[15];
     const int (*ef)[3];
     const int (*eg)[3];
@@ -717,6 +741,8 @@ void orc_set_bc(orc_grid *G, const int face_bc[6], const double T_wall[6], doubl
     G->gravity_axis = gravity_axis;
     G->gbeta = gbeta;
 }
+
+void orc_set_g_option(orc_grid *G, int option) { G->g_option = option ? 1 : 0; }
 
 void orc_set_omegas(orc_grid *G, const double *om_f, const double *om_g)
 {
@@ -832,12 +858,12 @@ static void node_update(orc_grid *G, int x, int y, int z)
         double mac[3];
         orc_d2q9_macro(fo, F[0], F[1], mac);
         orc_d2q9_f_collide(fo, mac[0], mac[1], mac[2], F[0], F[1], G->om_f, ft);
-        orc_d2q9_g_collide(go, mac[1], mac[2], G->om_g, gt);
+        orc_d2q9_g_collide(go, mac[1], mac[2], G->om_g, G->g_option, gt);
     } else {
         double mac[4];
         orc_d3q27_macro(fo, F[0], F[1], F[2], mac);
         orc_d3q27_f_collide(fo, mac[0], mac[1], mac[2], mac[3], F[0], F[1], F[2], G->om_f, ft);
-        orc_d3q15_g_collide(go, mac[1], mac[2], mac[3], G->om_g, gt);
+        orc_d3q15_g_collide(go, mac[1], mac[2], mac[3], G->om_g, G->g_option, gt);
     }
     for (int a = 0; a < G->qf; ++a) G->f2[(long)a * G->n + i] = ft[a];
     for (int a = 0; a < G->qg; ++a) G->g2[(long)a * G->n + i] = gt[a];

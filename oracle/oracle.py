@@ -108,8 +108,9 @@ def lib():
         L.orc_d2q9_macro.argtypes = [dp, d, d, dp]
         L.orc_d3q27_macro.argtypes = [dp, d, d, d, dp]
         L.orc_d2q9_f_collide.argtypes = [dp, d, d, d, d, d, dp, dp]
-        L.orc_d2q9_g_collide.argtypes = [dp, d, d, dp, dp]
-        L.orc_d3q15_g_collide.argtypes = [dp, d, d, d, dp, dp]
+        L.orc_d2q9_g_collide.argtypes = [dp, d, d, dp, i, dp]
+        L.orc_d3q15_g_collide.argtypes = [dp, d, d, d, dp, i, dp]
+        L.orc_set_g_option.argtypes = [v, i]
         L.orc_d3q27_f_collide.argtypes = [dp, d, d, d, d, d, d, d, dp, dp]
         L.orc_equilibrium_f.argtypes = [i, d, d, d, d, dp]
         L.orc_equilibrium_g.argtypes = [i, d, d, d, d, dp]
@@ -208,13 +209,14 @@ def collide_f(f, rho, u, F, om):
     return out
 
 
-def collide_g(g, u, om):
+def collide_g(g, u, om, option: int = 0):
+    """Energy collision; option 0 = option-A attractors, 1 = option B (renormalized)."""
     g = _vec(g)
     out = np.zeros(g.size)
     if g.size == 9:
-        lib().orc_d2q9_g_collide(_p(g), u[0], u[1], _p(_vec(om, 9)), _p(out))
+        lib().orc_d2q9_g_collide(_p(g), u[0], u[1], _p(_vec(om, 9)), option, _p(out))
     else:
-        lib().orc_d3q15_g_collide(_p(g), u[0], u[1], u[2], _p(_vec(om, 15)), _p(out))
+        lib().orc_d3q15_g_collide(_p(g), u[0], u[1], u[2], _p(_vec(om, 15)), option, _p(out))
     return out
 
 
@@ -321,7 +323,7 @@ class Oracle:
     """
 
     def __init__(self, dim, nx, ny, nz=1, bc: BC | None = None, Ra=None, Pr=None, Ma=None,
-                 om_f=None, om_g=None, gbeta=None, init=True):
+                 om_f=None, om_g=None, gbeta=None, init=True, g_option: int = 0):
         self.dim = dim
         self.nx, self.ny, self.nz = nx, ny, (nz if dim == 3 else 1)
         self.qf, self.qg = (9, 9) if dim == 2 else (27, 15)
@@ -346,6 +348,8 @@ class Oracle:
         self.om_f, self.om_g = _vec(om_f, self.qf), _vec(om_g, self.qg)
         self.gbeta = 0.0 if gbeta is None else float(gbeta)
         lib().orc_set_omegas(self.h, _p(self.om_f), _p(self.om_g))
+        self.g_option = int(g_option)
+        lib().orc_set_g_option(self.h, self.g_option)
         faces = (ctypes.c_int * 6)(*self.bc.face)
         tw = _vec(self.bc.T_wall, 6)
         lib().orc_set_bc(self.h, faces, _p(tw), self.bc.T_ref, self.bc.gravity_axis, self.gbeta)

@@ -237,33 +237,53 @@ __device__ __forceinline__ void relax_f_d2q9_vjp(const RT D[3][3], RT drho, RT i
 }
 
 // Reverse of relax_g_d2q9 (full values): adjoints tb of eta~ -> adjoints nb of eta and of T.
+// t holds the forward post-collision moments eta~ (needed by the option-B attractors).
 template <class RT>
-__device__ __forceinline__ void relax_g_d2q9_vjp(const Coeffs2D<RT>& c, const RT tb[3][3],
-                                                 RT nb[3][3], RT& Tb)
+__device__ __forceinline__ void relax_g_d2q9_vjp(const Coeffs2D<RT>& c, const RT t[3][3], RT T,
+                                                 const RT tb[3][3], RT nb[3][3], RT& Tb)
 {
     const RT* o = c.om_g;
-    const RT one = RT(1), half = RT(0.5);
+    const RT one = RT(1), half = RT(0.5), two = RT(2);
     const RT cs2 = RT(1.0 / 3.0);
-    const RT c1 = RT(2.0 / 9.0), c2 = RT(1.0 / 6.0);     // (2/3) c_s^2, (1/2) c_s^2
     const RT a00 = tb[0][0], a10 = tb[0][1], a20 = tb[0][2];
     const RT a01 = tb[1][0], a11 = tb[1][1], a21 = tb[1][2];
     const RT a02 = tb[2][0], a12 = tb[2][1], a22 = tb[2][2];
-    // t21, t12, t22 with attractors from post-collision t01, t10, t20 + t02
-    const RT n21b = a21 * (one - o[6]);
-    const RT t01b = a01 + c1 * a21 * o[6];
-    const RT n12b = a12 * (one - o[7]);
-    const RT t10b = a10 + c1 * a12 * o[7];
-    const RT n22b = a22 * (one - o[8]);
-    const RT t20b = a20 + c2 * a22 * o[8];
-    const RT t02b = a02 + c2 * a22 * o[8];
+    // t21, t12, t22 = n + o (Mv - n) with attractors from the post-collision lower moments
+    const RT n21b = a21 * (one - o[6]), M21b = a21 * o[6];
+    const RT n12b = a12 * (one - o[7]), M12b = a12 * o[7];
+    const RT n22b = a22 * (one - o[8]), M22b = a22 * o[8];
+    RT t10b = a10, t01b = a01, t20b = a20, t02b = a02, t11b = a11;
+    if (c.gopt == 0) {
+        // Mv21 = (2/3) c_s^2 t01, Mv12 = (2/3) c_s^2 t10, Mv22 = (1/2) c_s^2 (t20 + t02)
+        const RT c1 = RT(2.0 / 9.0), c2 = RT(1.0 / 6.0);
+        t01b += c1 * M21b;
+        t10b += c1 * M12b;
+        t20b += c2 * M22b;
+        t02b += c2 * M22b;
+    } else {
+        // Mv21 = c23 (t20 t01 + 2 t11 t10), Mv12 = c23 (t02 t10 + 2 t11 t01),
+        // Mv22 = (t20 t02 + 2 t11^2) / T, c23 = 2 / (3 T)
+        const RT t10 = t[0][1], t01 = t[1][0], t20 = t[0][2], t02 = t[2][0], t11 = t[1][1];
+        const RT iT = one / T, c23 = RT(2.0 / 3.0) * iT;
+        const RT P21 = t20 * t01 + two * t11 * t10;
+        const RT P12 = t02 * t10 + two * t11 * t01;
+        const RT P22 = t20 * t02 + two * t11 * t11;
+        const RT g21 = M21b * c23, g12 = M12b * c23, g22 = M22b * iT;
+        t20b += g21 * t01 + g22 * t02;
+        t02b += g12 * t10 + g22 * t20;
+        t01b += g21 * t20 + two * g12 * t11;
+        t10b += two * g21 * t11 + g12 * t02;
+        t11b += two * (g21 * t10 + g12 * t01) + RT(4) * g22 * t11;
+        Tb += -(g21 * P21 + g12 * P12 + g22 * P22) * iT;
+    }
     const RT t2sb = half * (t20b + t02b), t2db = half * (t20b - t02b);
     const RT n2sb = t2sb * (one - o[3]);
-    Tb += t2sb * o[3] * RT(2) * cs2 + a00 * o[0];
+    Tb += t2sb * o[3] * two * cs2 + a00 * o[0];
     const RT n2db = t2db * (one - o[4]);
     nb[0][0] = a00 * (one - o[0]);
     nb[0][1] = t10b * (one - o[1]);
     nb[1][0] = t01b * (one - o[2]);
-    nb[1][1] = a11 * (one - o[5]);
+    nb[1][1] = t11b * (one - o[5]);
     nb[0][2] = n2sb + n2db;
     nb[2][0] = n2sb - n2db;
     nb[1][2] = n21b;
@@ -308,11 +328,16 @@ __device__ __forceinline__ void collide_vjp_d2q9(const RT pf[9], const RT pg[9],
 #pragma unroll
             for (int a = 0; a < 3; ++a) Tm[j][a] = N[j][a];
         relax_g_d2q9(Tm, T, c);
+        RT Tpost[3][3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Tpost[j][a] = Tm[j][a];
         unsweeps_fwd(Tm, Y, uy);
         RT Tb[3][3], Nb[3][3];
         unsweeps_vjp(Tm, Y, lg, ux, uy, Tb, uxb, uyb);
         RT Tfb = 0;
-        relax_g_d2q9_vjp(c, Tb, Nb, Tfb);
+        relax_g_d2q9_vjp(c, Tpost, T, Tb, Nb, Tfb);
         dTb += Tfb;
         sweeps_vjp(X, N, Nb, ux, uy, mg, uxb, uyb);
     }

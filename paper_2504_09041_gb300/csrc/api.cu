@@ -413,6 +413,11 @@ int lbm_set_param(lbm_handle h, const char* key, double v)
         }
         return LBM_OK;
     }
+    if (k == "g_attractors") {
+        if (!(v == 0.0 || v == 1.0)) return fail(h, LBM_EINVAL, "g_attractors must be 0 (option A) or 1 (option B)");
+        h->hc.gopt = (int)v;
+        return LBM_OK;
+    }
     if (k == "adjoint_fp64") {
         if (!(v == 0.0 || v == 1.0)) return fail(h, LBM_EINVAL, "adjoint_fp64 must be 0 or 1");
         h->adjoint_fp64 = (int)v;
@@ -465,6 +470,7 @@ int lbm_info(lbm_handle h, lbm_info_t* o)
     o->block_x = (int)b.x;
     o->block_y = (int)b.y;
     o->graph_steps = h->graph_steps;
+    o->g_attractors = h->hc.gopt;
     return LBM_OK;
 }
 

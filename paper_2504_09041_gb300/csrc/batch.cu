@@ -3,11 +3,12 @@
 //
 // The members' populations are concatenated in two buffers (f and g, each with its own A/B copy);
 // a device table holds every member's geometry, relaxation rates and buffer offset, and the
-// first index of its tiles.  The launch has (SM count x CTAs per SM) blocks; block b takes the
-// tiles b, b + gridDim.x, ... of the global tile list, finds the owning member by binary search,
-// stages its table entry in shared memory and runs the same node step as the single-box kernel
-// on one node per thread.  The tile shape and CTAs per SM come from lbm_batch_set_launch or from
-// the autotuner lbm_batch_tune; the time loop replays CUDA graphs like lbm_step.
+// first index of its tiles.  The launch has (SM count x CTAs per SM) blocks, all resident at
+// once; block b takes an equal contiguous share of the global tile list, stages the owning
+// member's table entry in shared memory (again only where its share crosses into the next
+// member) and runs the same node step as the single-box kernel on one node per thread.  The
+// tile shape and CTAs per SM come from lbm_batch_set_launch or from the autotuner
+// lbm_batch_tune; the time loop replays CUDA graphs like lbm_step.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -40,22 +41,23 @@ __global__ void __launch_bounds__(256)
 {
     using M = BatchMember<typename S::R>;
     __shared__ __align__(16) unsigned char mbuf[sizeof(M)];
-    __shared__ int cur;
     const M& m = *reinterpret_cast<const M*>(mbuf);
-    int held = -1;
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        if (threadIdx.x == 0) {
-            int lo = 0, hi = n_members - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (members[mid].tile0 <= t) lo = mid;
-                else hi = mid - 1;
-            }
-            cur = lo;
-        }
-        __syncthreads();
-        const int k = cur;
+    // block b owns the contiguous tile range [t0, t1): equal shares, the first `rem` blocks one more
+    const int per = n_tiles / (int)gridDim.x, rem = n_tiles % (int)gridDim.x;
+    const int t0 = (int)blockIdx.x * per + min((int)blockIdx.x, rem);
+    const int t1 = t0 + per + ((int)blockIdx.x < rem ? 1 : 0);
+    // owning member of t0 (every thread reads the same entries, so k is uniform in the block)
+    int lo = 0, hi = n_members - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&members[mid].tile0) <= t0) lo = mid;
+        else hi = mid - 1;
+    }
+    int k = lo, held = -1;
+    for (int t = t0; t < t1; ++t) {
+        while (k + 1 < n_members && __ldg(&members[k + 1].tile0) <= t) ++k;
         if (k != held) {
+            __syncthreads();   // every thread is done with the previous member's entry
             const unsigned* src = reinterpret_cast<const unsigned*>(members + k);
             unsigned* dst = reinterpret_cast<unsigned*>(mbuf);
             for (int w = threadIdx.x; w < (int)(sizeof(M) / 4); w += blockDim.x) dst[w] = src[w];
@@ -68,7 +70,6 @@ __global__ void __launch_bounds__(256)
         if (x < m.geo.nx && y < m.geo.ny)
             node_step_d2q9<S, unsigned>(fin + m.off, gin + m.off, fout + m.off, gout + m.off, m.geo, m.c,
                                         status + k, x, y);
-        __syncthreads();   // every thread is done with this tile's member entry
     }
 }
 

@@ -18,6 +18,7 @@ struct HostCoeffs {
     double om_g[15];
     double gbeta, T_ref;
     int gaxis;
+    int gopt;   // energy attractors of orders 3-4: 0 = option A, 1 = option B
 };
 
 size_t storage_bytes(int prec);
@@ -97,6 +98,7 @@ inline Coeffs<R, QF, QG> make_coeffs(const HostCoeffs& h)
     c.gbeta = R(h.gbeta);
     c.T_ref = R(h.T_ref);
     c.gaxis = h.gaxis;
+    c.gopt = h.gopt;
     return c;
 }
 

@@ -66,6 +66,7 @@ struct Coeffs {
     R om_g[QG];
     R gbeta, T_ref;
     int gaxis;    // 0, 1, 2
+    int gopt;     // energy attractors of orders 3-4: 0 = option A, 1 = option B (renormalized)
 };
 
 // Per-thread wall bookkeeping for the pull.  For an axis, "m" is a link whose source lies at

@@ -44,6 +44,23 @@ __device__ __forceinline__ void pull_d2q9(const typename S::T* __restrict__ fin,
     });
 }
 
+// The same pull at a node whose eight neighbours all lie inside the box: no wall and no
+// periodic wrap touches any link, so every population comes straight from its upwind node.
+template <class S, class Idx = size_t>
+__device__ __forceinline__ void pull_d2q9_interior(const typename S::T* __restrict__ fin,
+                                                   const typename S::T* __restrict__ gin,
+                                                   const Geometry& geo, int i, typename S::R T_ref,
+                                                   typename S::R f[9], typename S::R g[9])
+{
+    using R = typename S::R;
+    static_for<9>([&](auto A) {
+        constexpr int a = decltype(A)::value;
+        const Idx off = (Idx)a * geo.n + (i - (e9(a, 0) + e9(a, 1) * geo.nx));
+        f[a] = S::load_dev(fin, off, R(w9(a)));
+        g[a] = S::load_dev(gin, off, R(w9(a)) * T_ref);
+    });
+}
+
 // Flow collision (App. A Step 3; second-order sources vanish; sigma_12 carries the factor 2 of
 // Eq. forcing:2D) on the deviations: D[b][a] = kappa_ab - K_ab on entry, kappa~_ab - K_ab on exit.
 template <class R>
@@ -86,8 +103,9 @@ __device__ __forceinline__ void relax_f_d2q9(R D[3][3], R drho, R irho, R ux, R 
     D[2][0] = T02; D[2][1] = T12; D[2][2] = T22;
 }
 
-// Energy collision in central-moment space on full values (App. B Step 3, option-A attractors
-// Eq. MvT2D); n[b][a] holds eta_ab on entry and eta~_ab on exit.
+// Energy collision in central-moment space on full values (App. B Step 3); n[b][a] holds eta_ab
+// on entry and eta~_ab on exit.  The attractors of orders 3-4 come from the post-collision lower
+// moments: option A (Eq. MvT2D, c.gopt = 0) or the renormalized option B (Eq. MvT2DoptionB).
 template <class R>
 __device__ __forceinline__ void relax_g_d2q9(R n[3][3], R T, const Coeffs2D<R>& c)
 {
@@ -105,9 +123,18 @@ __device__ __forceinline__ void relax_g_d2q9(R n[3][3], R T, const Coeffs2D<R>& 
     const R t11 = n11 - c.om_g[5] * n11;
     const R t20 = R(0.5) * (t2s + t2d);
     const R t02 = R(0.5) * (t2s - t2d);
-    const R Mv21 = R(2.0 / 3.0 * cs2) * t01;
-    const R Mv12 = R(2.0 / 3.0 * cs2) * t10;
-    const R Mv22 = R(0.5 * cs2) * (t20 + t02);
+    R Mv21, Mv12, Mv22;
+    if (c.gopt == 0) {
+        Mv21 = R(2.0 / 3.0 * cs2) * t01;
+        Mv12 = R(2.0 / 3.0 * cs2) * t10;
+        Mv22 = R(0.5 * cs2) * (t20 + t02);
+    } else {
+        const R iT = R(1) / T;
+        const R c23 = R(2.0 / 3.0) * iT;
+        Mv21 = c23 * (t20 * t01 + R(2) * t11 * t10);
+        Mv12 = c23 * (t02 * t10 + R(2) * t11 * t01);
+        Mv22 = iT * (t20 * t02 + R(2) * t11 * t11);
+    }
     const R t21 = n21 + c.om_g[6] * (Mv21 - n21);
     const R t12 = n12 + c.om_g[7] * (Mv12 - n12);
     const R t22 = n22 + c.om_g[8] * (Mv22 - n22);
@@ -156,9 +183,13 @@ __device__ __forceinline__ void node_step_d2q9(const typename S::T* __restrict__
 {
     using R = typename S::R;
     const int i = x + geo.nx * y;
-    const NodeWalls<R> w = node_walls<R>(geo, x, y, 0, 2);
     R f[9], g[9];
-    pull_d2q9<S, Idx>(fin, gin, geo, w, i, c.T_ref, f, g);
+    if (x > 0 && x < geo.nx - 1 && y > 0 && y < geo.ny - 1) {
+        pull_d2q9_interior<S, Idx>(fin, gin, geo, i, c.T_ref, f, g);
+    } else {
+        const NodeWalls<R> w = node_walls<R>(geo, x, y, 0, 2);
+        pull_d2q9<S, Idx>(fin, gin, geo, w, i, c.T_ref, f, g);
+    }
 
     // rho = 1 + sum delta, rho u = sum delta e + F/2, T = T_o + sum gamma (sum w = 1, sum w e = 0)
     const R dT = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];

@@ -60,6 +60,24 @@ __device__ __forceinline__ void pull_d3q27_d3q15(const typename S::T* __restrict
     });
 }
 
+// The same pull at a node whose 26 neighbours all lie inside the box (no wall, no wrap).
+template <class S, class Idx = size_t>
+__device__ __forceinline__ void pull_d3q27_d3q15_interior(const typename S::T* __restrict__ fin,
+                                                          const typename S::T* __restrict__ gin,
+                                                          const Geometry& geo, int i,
+                                                          typename S::R T_ref, typename S::R f[27],
+                                                          typename S::R g[15])
+{
+    using R = typename S::R;
+    static_for<27>([&](auto A) {
+        constexpr int a = decltype(A)::value;
+        const int s = i - (e27(a, 0) + e27(a, 1) * geo.nx + e27(a, 2) * geo.nxy);
+        f[a] = S::load_dev(fin, (Idx)a * geo.n + s, R(w27(a)));
+        constexpr int b = g15_of_27(a);
+        if constexpr (b >= 0) g[b] = S::load_dev(gin, (Idx)b * geo.n + s, R(w15(b)) * T_ref);
+    });
+}
+
 // Flow collision (reading R6 of the oracle notes) on the deviations: D[c][b][a] = kappa_abc - K_abc
 // on entry, kappa~_abc - K_abc on exit.  Rate slots follow the moment order of Sec. 5.2; slot 7
 // relaxes the trace (bulk), slots 8 and 9 the deviators kappa_200 - kappa_020, kappa_200 - kappa_002.
@@ -223,7 +241,8 @@ __device__ __forceinline__ void from_central_d3q27(R p[3][3][3], R f[27], R ux, 
 // D3Q15 energy collision, App. C Steps 1-5 with option-A attractors (Eq. g-attractorsD3Q15optionA).
 // Moment order (000, 100, 010, 001, 110, 101, 011, 200, 020, 002, 120, 012, 201, 111, 220).
 template <class R>
-__device__ __forceinline__ void collide_g_d3q15(R g[15], R T, R ux, R uy, R uz, const R om[15])
+__device__ __forceinline__ void collide_g_d3q15(R g[15], R T, R ux, R uy, R uz, const R om[15],
+                                                int gopt)
 {
     constexpr double cs2 = 1.0 / 3.0;
     // Step 1: raw moments.  Axis pairs ...
@@ -280,11 +299,28 @@ __device__ __forceinline__ void collide_g_d3q15(R g[15], R T, R ux, R uy, R uz, 
     const R t200 = n200 + om[7] * (R(cs2) * T - n200);
     const R t020 = n020 + om[8] * (R(cs2) * T - n020);
     const R t002 = n002 + om[9] * (R(cs2) * T - n002);
-    const R t120 = n120 + om[10] * (R(2.0 / 3.0 * cs2) * t100 - n120);
-    const R t012 = n012 + om[11] * (R(2.0 / 3.0 * cs2) * t010 - n012);
-    const R t201 = n201 + om[12] * (R(2.0 / 3.0 * cs2) * t001 - n201);
-    const R t111 = n111 - om[13] * n111;
-    const R t220 = n220 + om[14] * (R(0.5 * cs2) * (t200 + t020) - n220);
+    // attractors of orders 3-4 from the post-collision moments: option A or option B
+    R M120, M012, M201, M111, M220;
+    if (gopt == 0) {
+        M120 = R(2.0 / 3.0 * cs2) * t100;
+        M012 = R(2.0 / 3.0 * cs2) * t010;
+        M201 = R(2.0 / 3.0 * cs2) * t001;
+        M111 = R(0);
+        M220 = R(0.5 * cs2) * (t200 + t020);
+    } else {
+        const R iT = R(1) / T;
+        const R c23 = R(2.0 / 3.0) * iT;
+        M120 = c23 * (t020 * t100 + R(2) * t110 * t010);
+        M012 = c23 * (t002 * t010 + R(2) * t011 * t001);
+        M201 = c23 * (t200 * t001 + R(2) * t101 * t100);
+        M111 = c23 * (t110 * t001 + t011 * t100 + t101 * t010);
+        M220 = iT * (t200 * t020 + R(2) * t110 * t110);
+    }
+    const R t120 = n120 + om[10] * (M120 - n120);
+    const R t012 = n012 + om[11] * (M012 - n012);
+    const R t201 = n201 + om[12] * (M201 - n201);
+    const R t111 = n111 + om[13] * (M111 - n111);
+    const R t220 = n220 + om[14] * (M220 - n220);
 
     // Step 4: raw moments from central moments (the inverse of Step 2 in reverse order).
     const R q000 = t000;
@@ -347,9 +383,13 @@ __device__ __forceinline__ void node_step_d3q27(const typename S::T* __restrict_
 {
     using R = typename S::R;
     const int i = x + geo.nx * y + geo.nxy * z;
-    const NodeWalls<R> w = node_walls<R>(geo, x, y, z, 3);
     R f[27], g[15];
-    pull_d3q27_d3q15<S, Idx>(fin, gin, geo, w, i, c.T_ref, f, g);
+    if (x > 0 && x < geo.nx - 1 && y > 0 && y < geo.ny - 1 && z > 0 && z < geo.nz - 1) {
+        pull_d3q27_d3q15_interior<S, Idx>(fin, gin, geo, i, c.T_ref, f, g);
+    } else {
+        const NodeWalls<R> w = node_walls<R>(geo, x, y, z, 3);
+        pull_d3q27_d3q15<S, Idx>(fin, gin, geo, w, i, c.T_ref, f, g);
+    }
 
     // rho = 1 + sum delta, rho u = sum delta e + F/2, T = T_o + sum gamma
     R dT = g[0];
@@ -389,7 +429,7 @@ __device__ __forceinline__ void node_step_d3q27(const typename S::T* __restrict_
         constexpr int b = decltype(B)::value;
         g[b] += R(w15(b)) * c.T_ref;
     });
-    collide_g_d3q15(g, T, ux, uy, uz, c.om_g);
+    collide_g_d3q15(g, T, ux, uy, uz, c.om_g, c.gopt);
 
     static_for<27>([&](auto A) {
         constexpr int a = decltype(A)::value;

@@ -49,17 +49,18 @@ def walls_pair(kind: str, dim: int, seed=0, perturb=0.0):
 
 
 def make_pair(dim, nx, ny, nz=1, kind="cavity", precision="fp64", rates_seed=None, gbeta=None,
-              Ra=1e4, Pr=0.71, Ma=0.1, seed=0, perturb=0.0, rate_range=(0.6, 1.9)):
+              Ra=1e4, Pr=0.71, Ma=0.1, seed=0, perturb=0.0, rate_range=(0.6, 1.9), g_option=0):
     lat = "d2q9" if dim == 2 else "d3q27"
     wl, wo = walls_pair(kind, dim, seed, perturb)
     gpu = L.Lattice(lat, nx, ny, nz, Ra=Ra, Pr=Pr, Ma=Ma, walls=wl, precision=precision)
+    gpu.set_param("g_attractors", g_option)
     if rates_seed is None:
-        ora = O.Oracle(dim, nx, ny, nz, bc=wo, Ra=Ra, Pr=Pr, Ma=Ma)
+        ora = O.Oracle(dim, nx, ny, nz, bc=wo, Ra=Ra, Pr=Pr, Ma=Ma, g_option=g_option)
     else:
         qf, qg = (9, 9) if dim == 2 else (27, 15)
         om_f = synth.rates(rates_seed, qf, *rate_range)
         om_g = synth.rates(rates_seed + 1, qg, *rate_range)
-        ora = O.Oracle(dim, nx, ny, nz, bc=wo, om_f=om_f, om_g=om_g, gbeta=gbeta)
+        ora = O.Oracle(dim, nx, ny, nz, bc=wo, om_f=om_f, om_g=om_g, gbeta=gbeta, g_option=g_option)
         gpu.set_omegas(om_f, om_g)
         gpu.set_param("gbeta", gbeta)
     return gpu, ora
@@ -185,6 +186,32 @@ def test_fp64_step_parity_3d(kind, shape):
     assert pop_error(gpu, ora) <= 1e-12
 
 
+@pytest.mark.parametrize("dim,shape", [(2, (1, 37, 131)), (3, (13, 21, 37))])
+def test_fp64_step_parity_option_b(dim, shape):
+    """The renormalized option-B energy attractors (Eq. MvT2DoptionB, Sec. 5.3 D3Q15 list), with
+    random second-order rates so that they differ from option A."""
+    nz, ny, nx = shape
+    kind = "rb" if dim == 2 else "cavity"
+    rr = (0.6, 1.9) if dim == 2 else (0.7, 1.7)
+    gpu, ora = make_pair(dim, nx, ny, nz, kind=kind, rates_seed=51, gbeta=3e-3, rate_range=rr,
+                         g_option=1)
+    assert gpu.info().g_attractors == 1
+    randomize(gpu, ora, 8, scale=0.3 if dim == 2 else 0.05)
+    gpu.step(1); ora.step(1)
+    assert pop_error(gpu, ora) <= 1e-14
+    gpu.step(99); ora.step(99)
+    gpu.sync()
+    assert pop_error(gpu, ora) <= 1e-12
+
+
+def test_g_attractors_parameter_is_validated():
+    gpu = L.Lattice("d2q9", 8, 8, Ra=1e4, precision="fp32")
+    for bad in (-1, 2, 0.5):
+        with pytest.raises(L.LbmError):
+            gpu.set_param("g_attractors", bad)
+    assert gpu.info().g_attractors == 0
+
+
 @pytest.mark.parametrize("dim,shape", [(2, (1, 1, 1)), (2, (1, 2, 2)), (2, (1, 3, 1)),
                                        (3, (2, 2, 2)), (3, (1, 3, 2)), (3, (3, 1, 1))])
 def test_fp64_degenerate_boxes(dim, shape):
@@ -269,10 +296,11 @@ def test_divergence_is_reported_without_a_fault():
 # ---------------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("dim,shape", [(2, (1, 70, 150)), (3, (13, 21, 37))])
-def test_fp32_fields_within_1e5(dim, shape):
+@pytest.mark.parametrize("g_option", [0, 1])
+def test_fp32_fields_within_1e5(dim, shape, g_option):
     nz, ny, nx = shape
     gpu, ora = make_pair(dim, nx, ny, nz, kind="cavity", precision="fp32", rates_seed=51, gbeta=3e-3,
-                         rate_range=(0.6, 1.9) if dim == 2 else (0.7, 1.7))
+                         rate_range=(0.6, 1.9) if dim == 2 else (0.7, 1.7), g_option=g_option)
     randomize(gpu, ora, 9, scale=0.3 if dim == 2 else 0.05)
     # the FP64 oracle starts from the FP32-rounded state the GPU holds
     f, g = gpu.get_populations()

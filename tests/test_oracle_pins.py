@@ -239,13 +239,27 @@ def test_d2q9_f_collision_is_fp_relaxation(seed):
         _check_relaxation(pre, post, Mv, om[j], sig[j], j)
 
 
+def _g_diffusion(option, post, M, T):
+    """D-hat' used for the attractors of orders above 2: option A keeps c_s^2-hat (Eq.
+    Dij2D_goptionA), option B renormalizes with the post-collision second moments (Eq. Dij2D_g
+    and its 3D counterpart)."""
+    c = 1 / 3
+    if option == 0:
+        return {"xx": c, "yy": c, "zz": c, "xy": 0.0, "xz": 0.0, "yz": 0.0}
+    k = {mnp: post[j] for j, mnp in enumerate(M)}
+    g = lambda mnp: k.get(mnp, 0.0) / T
+    return {"xx": g((2, 0, 0)), "yy": g((0, 2, 0)), "zz": g((0, 0, 2)), "xy": g((1, 1, 0)),
+            "xz": g((1, 0, 1)), "yz": g((0, 1, 1))}
+
+
+@pytest.mark.parametrize("option", [0, 1])
 @pytest.mark.parametrize("seed", range(6))
-def test_d2q9_g_collision_is_fp_relaxation(seed):
+def test_d2q9_g_collision_is_fp_relaxation(seed, option):
     rng = np.random.default_rng(200 + seed)
     u = np.array([*rng.uniform(-0.1, 0.1, 2), 0.0])
     g = random_pops(rng, O.equilibrium_g(2, 0.7, u[:2]), 0.3)
     om = rng.uniform(0.3, 1.9, 9)
-    gt = O.collide_g(g, u[:2], om)
+    gt = O.collide_g(g, u[:2], om, option)
     pre = moments_by_definition(g, O.E_D2Q9, O.M_D2Q9, u)
     post = moments_by_definition(gt, O.E_D2Q9, O.M_D2Q9, u)
     T = pre[0]
@@ -257,28 +271,47 @@ def test_d2q9_g_collision_is_fp_relaxation(seed):
                                               abs=1e-13)
     assert post[3] - post[4] == pytest.approx((pre[3] - pre[4]) * (1 - om[4]), abs=1e-13)
     _check_relaxation(pre, post, 0.0, om[5], 0.0, 5)
-    # option A: D-hat' = c_s^2-hat delta for all orders; lower moments are post-collision
+    # orders 3-4 from the post-collision lower moments and the option's D-hat'
     lower = {mnp: post[j] for j, mnp in enumerate(O.M_D2Q9)}
-    D = {"xx": c, "yy": c, "zz": c, "xy": 0.0, "xz": 0.0, "yz": 0.0}
+    D = _g_diffusion(option, post, O.M_D2Q9, T)
     for j in (6, 7, 8):
         _check_relaxation(pre, post, recurrence_attractor(O.M_D2Q9[j], lower, D), om[j], 0.0, j)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_g_options_coincide_when_second_moments_reach_equilibrium(dim):
+    """With the second-order energy rates at 1 the post-collision second moments are exactly
+    c_s^2-hat T (diagonal) and 0 (off-diagonal), so option B's D-hat' = eta~ / T equals option A's
+    and the two collisions agree; with other second-order rates they differ."""
+    rng = np.random.default_rng(500 + dim)
+    q = 9 if dim == 2 else 15
+    u = rng.uniform(-0.1, 0.1, 3)[:dim]
+    g = random_pops(rng, O.equilibrium_g(dim, 0.7, u), 0.3)
+    om = rng.uniform(0.3, 1.9, q)
+    second = [3, 4, 5] if dim == 2 else [4, 5, 6, 7, 8, 9]
+    om[second] = 1.0
+    np.testing.assert_allclose(O.collide_g(g, u, om, 1), O.collide_g(g, u, om, 0), rtol=0,
+                               atol=1e-15)
+    om[second[0]] = 1.4
+    assert np.abs(O.collide_g(g, u, om, 1) - O.collide_g(g, u, om, 0)).max() > 1e-6
+
+
+@pytest.mark.parametrize("option", [0, 1])
 @pytest.mark.parametrize("seed", range(4))
-def test_d3q15_g_collision_is_fp_relaxation(seed):
-    """Pins reading R3 (eta^Mv_012 carries c_s^2-hat)."""
+def test_d3q15_g_collision_is_fp_relaxation(seed, option):
+    """Pins reading R3 (eta^Mv_012 carries c_s^2-hat) and the option-B list."""
     rng = np.random.default_rng(300 + seed)
     u = rng.uniform(-0.1, 0.1, 3)
     g = random_pops(rng, O.equilibrium_g(3, 0.7, u), 0.3)
     om = rng.uniform(0.3, 1.9, 15)
-    gt = O.collide_g(g, u, om)
+    gt = O.collide_g(g, u, om, option)
     pre = moments_by_definition(g, O.E_D3Q15, O.M_D3Q15, u)
     post = moments_by_definition(gt, O.E_D3Q15, O.M_D3Q15, u)
     T = pre[0]
     assert post[0] == pytest.approx(T, abs=1e-14)
     c = 1 / 3
     lower = {mnp: post[j] for j, mnp in enumerate(O.M_D3Q15)}
-    D = {"xx": c, "yy": c, "zz": c, "xy": 0.0, "xz": 0.0, "yz": 0.0}
+    D = _g_diffusion(option, post, O.M_D3Q15, T)
     for j, mnp in enumerate(O.M_D3Q15):
         if j == 0:
             continue
