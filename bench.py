@@ -51,6 +51,11 @@ def reduce_max(value: float, world: int) -> float:
     return float(t.item())
 
 
+def job_mlups(nodes_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: the node updates of all ranks over the slowest rank's time."""
+    return nodes_per_rank * steps * world / seconds / 1e6
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -247,12 +252,12 @@ def run_gpu(args):
     if rank != 0:
         return None
 
-    mlups = n * args.steps * world / t_max / 1e6
+    mlups = job_mlups(n, args.steps, world, t_max)
     step_s = t_steps / args.steps
     achieved = bpn * n / step_s / 1e9
     peak, peak_kind = hbm_peak()
     traffic = committed_traffic()
-    e2e = n * args.steps * world / t_e2e / 1e6
+    e2e = job_mlups(n, args.steps, world, t_e2e)
     line = {
         "metric": METRIC,
         "value": round(mlups, 2),

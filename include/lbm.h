@@ -271,7 +271,7 @@ typedef struct {
     long long total_nodes;          /* sum of nx * ny over the members */
     int n_tiles;                    /* tiles of the current tile shape over all members */
     int tile_x, tile_y;             /* nodes per tile along x and y (one node per thread) */
-    int ctas_per_sm;                /* resident blocks the launch asks for on each SM */
+    int ctas_per_sm;                /* blocks per SM of the launch (the resident count if 0 was set) */
     int grid;                       /* blocks of one step launch: min(n_tiles, SMs * ctas_per_sm) */
     int graph_steps;                /* steps per CUDA graph replay (0 = plain launches) */
     long long steps;                /* time steps taken */
@@ -291,14 +291,15 @@ LBM_API int lbm_batch_destroy(lbm_batch b);
 LBM_API int lbm_batch_set_stream(lbm_batch b, void* stream);
 
 /* Launch shape of the step: tiles of tile_x x tile_y nodes (tile_x in {32, 64, 128, 256},
- * tile_x * tile_y <= 256 threads), ctas_per_sm blocks per SM (ctas_per_sm * threads <= 2048), and
+ * tile_x * tile_y <= 256 threads), ctas_per_sm blocks per SM (1..64; 0 = as many as the SM holds
+ * at once, so that every block is resident and takes one equal share of the tiles), and
  * graph_steps steps per CUDA graph replay (0..4096, rounded up to even; 0 = plain launches).
- * Default 64 x 2 tiles, 8 CTAs per SM, 32 graph steps.  Errors: LBM_EINVAL for another shape. */
+ * Default 64 x 2 tiles, ctas_per_sm 0, 32 graph steps.  Errors: LBM_EINVAL for another shape. */
 LBM_API int lbm_batch_set_launch(lbm_batch b, int tile_x, int tile_y, int ctas_per_sm, int graph_steps);
 
-/* Autotuner: time trial_steps steps of every valid (tile shape, CTAs per SM) pair from a fixed
- * list on a device copy of the current populations, keep the fastest, and report it through the
- * optional outputs.  The batch's own state and step count are unchanged (divergence flags are
+/* Autotuner: time trial_steps steps of every tile shape of a fixed list, each with half, all and
+ * twice the blocks per SM that the SM holds at once (CUDA occupancy API), on a device copy of the
+ * current populations; keep the fastest and report it through the optional outputs.  The batch's own state and step count are unchanged (divergence flags are
  * cleared).  Needs device memory for two extra copies of the populations (LBM_ENOMEM otherwise). */
 LBM_API int lbm_batch_tune(lbm_batch b, int trial_steps, int* tile_x, int* tile_y, int* ctas_per_sm);
 

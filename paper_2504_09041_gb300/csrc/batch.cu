@@ -32,8 +32,15 @@ struct BatchMember {
     int tiles_x;              // tiles along x
 };
 
+// FP32 registers: at least 5 blocks of 256 threads (48 registers, no spills), i.e. 40 resident
+// warps per SM for the memory pipeline; FP64 keeps the compiler's choice.
 template <class S>
-__global__ void __launch_bounds__(256)
+struct BatchBounds {
+    static constexpr int kMinBlocks = sizeof(typename S::R) == 8 ? 1 : 5;
+};
+
+template <class S>
+__global__ void __launch_bounds__(256, BatchBounds<S>::kMinBlocks)
     batch_step_d2q9_kernel(const typename S::T* __restrict__ fin, const typename S::T* __restrict__ gin,
                            typename S::T* __restrict__ fout, typename S::T* __restrict__ gout,
                            const BatchMember<typename S::R>* __restrict__ members, int n_members,
@@ -73,6 +80,18 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Blocks of `threads` threads of the step kernel that fit on one SM at once.
+template <class S>
+static int resident_blocks(int threads)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_d2q9_kernel<S>, threads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
+
 template <class S>
 static cudaError_t launch_batch(const void* fin, const void* gin, void* fout, void* gout,
                                 const void* members, int n_members, int n_tiles, int tile_x,
@@ -100,7 +119,7 @@ struct lbm_batch_s {
     unsigned* status = nullptr;
     double *nu_profile = nullptr, *nu_scratch = nullptr, *nu_result = nullptr;
     unsigned* ticket = nullptr;
-    int n_tiles = 0, tile_x = 64, tile_y = 2, ctas_per_sm = 8, sms = 0;
+    int n_tiles = 0, tile_x = 64, tile_y = 2, ctas_per_sm = 0, sms = 0;
     cudaStream_t stream = nullptr, capture_stream = nullptr;
     int graph_steps = 32;
     unsigned gen = 1, graph_gen[2] = {0, 0};
@@ -202,10 +221,20 @@ int upload_table(lbm_batch_s* b)
     return LBM_OK;
 }
 
+int max_resident(int prec, int threads);
+
+// Blocks of one step launch: ctas_per_sm blocks per SM (0 = as many as are resident at once),
+// at most one per tile.
+int grid_of(lbm_batch_s* b)
+{
+    const int cps = b->ctas_per_sm > 0 ? b->ctas_per_sm : max_resident(b->prec, b->tile_x * b->tile_y);
+    return std::max(1, std::min(b->n_tiles, b->sms * cps));
+}
+
 cudaError_t launch_one(lbm_batch_s* b, const void* fin, const void* gin, void* fout, void* gout,
                        cudaStream_t st)
 {
-    const int grid = std::max(1, std::min(b->n_tiles, b->sms * b->ctas_per_sm));
+    const int grid = grid_of(b);
     switch (b->prec) {
     case lbm::kF64: return lbm::launch_batch<lbm::StoreF64>(fin, gin, fout, gout, b->members, b->count, b->n_tiles, b->tile_x, b->tile_y, grid, b->status, st);
     case lbm::kF32: return lbm::launch_batch<lbm::StoreF32>(fin, gin, fout, gout, b->members, b->count, b->n_tiles, b->tile_x, b->tile_y, grid, b->status, st);
@@ -214,11 +243,20 @@ cudaError_t launch_one(lbm_batch_s* b, const void* fin, const void* gin, void* f
     return cudaErrorInvalidValue;
 }
 
+int max_resident(int prec, int threads)
+{
+    switch (prec) {
+    case lbm::kF64: return lbm::resident_blocks<lbm::StoreF64>(threads);
+    case lbm::kF32: return lbm::resident_blocks<lbm::StoreF32>(threads);
+    default: return lbm::resident_blocks<lbm::StoreF16S>(threads);
+    }
+}
+
 int valid_launch(int tx, int ty, int cps)
 {
     const int threads = tx * ty;
     return (tx == 32 || tx == 64 || tx == 128 || tx == 256) && ty >= 1 && threads <= 256 &&
-           cps >= 1 && cps * threads <= 2048;
+           cps >= 0 && cps <= 64;
 }
 
 size_t elem_bytes(int prec) { return lbm::storage_bytes(prec); }
@@ -400,8 +438,8 @@ int lbm_batch_tune(lbm_batch b, int trial_steps, int* tile_x, int* tile_y, int* 
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // each tile shape with half, all and twice the blocks that are resident on an SM at once
     const int shapes[][2] = {{32, 2}, {32, 4}, {64, 1}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}};
-    const int ctas[] = {2, 4, 8, 16, 32};
     const int keep[3] = {b->tile_x, b->tile_y, b->ctas_per_sm};
     float best = INFINITY;
     int bx = keep[0], by = keep[1], bc = keep[2];
@@ -409,6 +447,8 @@ int lbm_batch_tune(lbm_batch b, int trial_steps, int* tile_x, int* tile_y, int* 
     cudaMemcpyAsync(tf[0], b->f[b->cur], bytes, cudaMemcpyDeviceToDevice, b->stream);
     cudaMemcpyAsync(tg[0], b->g[b->cur], bytes, cudaMemcpyDeviceToDevice, b->stream);
     for (auto& sh : shapes) {
+        const int occ = max_resident(b->prec, sh[0] * sh[1]);
+        const int ctas[3] = {std::max(1, occ / 2), occ, 2 * occ};
         for (int cps : ctas) {
             if (!valid_launch(sh[0], sh[1], cps)) continue;
             b->tile_x = sh[0];
@@ -541,8 +581,8 @@ int lbm_batch_info(lbm_batch b, lbm_batch_info_t* o)
     o->n_tiles = b->n_tiles;
     o->tile_x = b->tile_x;
     o->tile_y = b->tile_y;
-    o->ctas_per_sm = b->ctas_per_sm;
-    o->grid = std::max(1, std::min(b->n_tiles, b->sms * b->ctas_per_sm));
+    o->ctas_per_sm = b->ctas_per_sm > 0 ? b->ctas_per_sm : max_resident(b->prec, b->tile_x * b->tile_y);
+    o->grid = grid_of(b);
     o->graph_steps = b->graph_steps;
     o->steps = b->steps;
     o->bytes_per_node_update = 2.0 * 18 * (double)elem_bytes(b->prec);

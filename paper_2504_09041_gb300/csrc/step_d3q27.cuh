@@ -443,7 +443,7 @@ __device__ __forceinline__ void node_step_d3q27(const typename S::T* __restrict_
 
 template <class S>
 struct Launch3D {
-    static constexpr int kMinBlocks = sizeof(typename S::R) == 8 ? 1 : 2;
+    static constexpr int kMinBlocks = sizeof(typename S::R) == 8 ? 1 : 3;
 };
 
 template <class S, class Idx>

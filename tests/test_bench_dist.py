@@ -1,0 +1,68 @@
+"""The multi-rank path of bench.py on CPU: two gloo ranks (replicas, weak scaling).
+
+Each rank of a torchrun launch advances its own cavity; the ranks meet only at a barrier and at
+the max-reduction of their timed windows.  These tests run that host logic with the gloo backend
+and world size 2, and check the reference arm's rank handling.
+"""
+import argparse
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        r, w, local = bench.dist_env()
+        assert (r, w, local) == (rank, world, rank)
+        bench.barrier(world)
+        # each rank's timed window; the job is as slow as its slowest rank
+        t = 0.5 + 0.25 * rank
+        t_max = bench.reduce_max(t, world)
+        args = argparse.Namespace(steps=1, warmup=0)
+        ref = bench.run_reference(args)
+        out[rank] = (t_max, bench.job_mlups(1000, 10, world, t_max), ref is None)
+        bench.barrier(world)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_the_slowest_window():
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        procs = [ctx.Process(target=_rank_main, args=(r, world, port, out)) for r in range(world)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=300)
+        assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+        res = dict(out)
+    assert res[0][0] == res[1][0] == 0.75
+    # whole-job value: both ranks' node updates over the slowest window
+    assert res[0][1] == pytest.approx(1000 * 10 * 2 / 0.75 / 1e6)
+    # the reference arm runs on rank 0 only
+    assert res[0][2] is False and res[1][2] is True
+
+
+def test_single_rank_helpers_are_identities():
+    assert bench.reduce_max(3.5, 1) == 3.5
+    bench.barrier(1)
+    assert bench.job_mlups(100, 10, 1, 2.0) == pytest.approx(5e-4)

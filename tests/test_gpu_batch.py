@@ -102,7 +102,8 @@ def test_fp64_members_match_oracle():
     b.close()
 
 
-@pytest.mark.parametrize("shape", [(32, 1, 2), (32, 4, 8), (64, 1, 16), (128, 2, 4), (256, 1, 8)])
+@pytest.mark.parametrize("shape", [(32, 1, 2), (32, 4, 8), (64, 1, 16), (128, 2, 4), (256, 1, 8),
+                                   (64, 2, 0)])
 def test_launch_shape_does_not_change_results(shape):
     ref = make_batch("fp32")
     states = perturb_members(ref, 20)
@@ -113,7 +114,8 @@ def test_launch_shape_does_not_change_results(shape):
     b.set_launch(*shape, graph_steps=8)
     b.step(40)
     inf = b.info()
-    assert (inf.tile_x, inf.tile_y, inf.ctas_per_sm, inf.graph_steps) == (*shape, 8)
+    assert (inf.tile_x, inf.tile_y, inf.graph_steps) == (*shape[:2], 8)
+    assert inf.ctas_per_sm == shape[2] or (shape[2] == 0 and inf.ctas_per_sm >= 1)
     for k in range(b.count):
         fa, ga = ref.get_populations(k)
         fb, gb = b.get_populations(k)
@@ -147,7 +149,7 @@ def test_autotuner_keeps_state_and_picks_a_valid_shape():
     tx, ty, cps = b.tune(4)
     inf = b.info()
     assert (inf.tile_x, inf.tile_y, inf.ctas_per_sm) == (tx, ty, cps)
-    assert tx in (32, 64, 128, 256) and tx * ty <= 256 and cps * tx * ty <= 2048
+    assert tx in (32, 64, 128, 256) and tx * ty <= 256 and 1 <= cps <= 64
     assert inf.steps == 3
     for k in range(b.count):
         f, g = b.get_populations(k)
@@ -199,7 +201,7 @@ def test_divergence_is_flagged_per_member():
 
 def test_invalid_launch_shapes_are_rejected():
     b = make_batch("fp32")
-    for bad in [(48, 2, 8), (64, 8, 8), (256, 1, 16), (64, 2, 0)]:
+    for bad in [(48, 2, 8), (64, 8, 8), (256, 1, 65), (64, 2, -1)]:
         with pytest.raises(L.LbmError):
             b.set_launch(*bad)
     with pytest.raises(L.LbmError):
