@@ -112,6 +112,32 @@ __device__ __forceinline__ NodeWalls<R> node_walls(const Geometry& g, int x, int
     return w;
 }
 
+// The same bookkeeping for a node whose y and z neighbours all lie inside the box: only the x
+// axis can wrap or meet a wall, and the y / z entries are compile-time zeros that fold away.
+template <class R>
+__device__ __forceinline__ NodeWalls<R> node_walls_x(const Geometry& g, int x, int y, int z)
+{
+    NodeWalls<R> w;
+    const bool lo = x == 0, hi = x == g.nx - 1;
+    const bool per = g.kind[0] == kPeriodic;
+    w.wrap_m[0] = (lo && per) ? g.nx : 0;
+    w.wrap_p[0] = (hi && per) ? -g.nx : 0;
+    w.out_m[0] = lo && !per;
+    w.out_p[0] = hi && !per;
+    w.fix_m[0] = w.out_m[0] && g.kind[0] == kFixedT;
+    w.fix_p[0] = w.out_p[0] && g.kind[1] == kFixedT;
+    w.tw_m[0] = w.fix_m[0] ? R(wall_temperature(g, 0, x, y, z)) : R(0);
+    w.tw_p[0] = w.fix_p[0] ? R(wall_temperature(g, 1, x, y, z)) : R(0);
+#pragma unroll
+    for (int ax = 1; ax < 3; ++ax) {
+        w.wrap_m[ax] = w.wrap_p[ax] = 0;
+        w.out_m[ax] = w.out_p[ax] = false;
+        w.fix_m[ax] = w.fix_p[ax] = false;
+        w.tw_m[ax] = w.tw_p[ax] = R(0);
+    }
+    return w;
+}
+
 // Source of the link arriving at node i along (EX, EY, EZ) after the walls.  Returns the
 // linear index of the source node.  *out is set when the source lies beyond a wall; *dir is
 // set when one of the crossed walls has a fixed temperature, and *tw is then the temperature of

@@ -184,7 +184,17 @@ __device__ __forceinline__ void node_step_d2q9(const typename S::T* __restrict__
     using R = typename S::R;
     const int i = x + geo.nx * y;
     R f[9], g[9];
-    if (x > 0 && x < geo.nx - 1 && y > 0 && y < geo.ny - 1) {
+    // Which pull: decided per warp where possible, so that a warp holding an x-wall node of an
+    // interior row runs one x-only pull instead of both the interior and the general pull.
+    const bool y_in = y > 0 && y < geo.ny - 1;
+    const bool in = y_in && x > 0 && x < geo.nx - 1;
+    const unsigned lanes = __activemask();
+    if (__all_sync(lanes, in)) {
+        pull_d2q9_interior<S, Idx>(fin, gin, geo, i, c.T_ref, f, g);
+    } else if (__all_sync(lanes, y_in)) {
+        const NodeWalls<R> w = node_walls_x<R>(geo, x, y, 0);
+        pull_d2q9<S, Idx>(fin, gin, geo, w, i, c.T_ref, f, g);
+    } else if (in) {
         pull_d2q9_interior<S, Idx>(fin, gin, geo, i, c.T_ref, f, g);
     } else {
         const NodeWalls<R> w = node_walls<R>(geo, x, y, 0, 2);

@@ -384,7 +384,17 @@ __device__ __forceinline__ void node_step_d3q27(const typename S::T* __restrict_
     using R = typename S::R;
     const int i = x + geo.nx * y + geo.nxy * z;
     R f[27], g[15];
-    if (x > 0 && x < geo.nx - 1 && y > 0 && y < geo.ny - 1 && z > 0 && z < geo.nz - 1) {
+    // Which pull: decided per warp where possible, so that a warp holding an x-wall node of an
+    // interior row runs one x-only pull instead of both the interior and the general pull.
+    const bool yz_in = y > 0 && y < geo.ny - 1 && z > 0 && z < geo.nz - 1;
+    const bool in = yz_in && x > 0 && x < geo.nx - 1;
+    const unsigned lanes = __activemask();
+    if (__all_sync(lanes, in)) {
+        pull_d3q27_d3q15_interior<S, Idx>(fin, gin, geo, i, c.T_ref, f, g);
+    } else if (__all_sync(lanes, yz_in)) {
+        const NodeWalls<R> w = node_walls_x<R>(geo, x, y, z);
+        pull_d3q27_d3q15<S, Idx>(fin, gin, geo, w, i, c.T_ref, f, g);
+    } else if (in) {
         pull_d3q27_d3q15_interior<S, Idx>(fin, gin, geo, i, c.T_ref, f, g);
     } else {
         const NodeWalls<R> w = node_walls<R>(geo, x, y, z, 3);
