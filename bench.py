@@ -304,6 +304,20 @@ def run_gpu(args):
     return line
 
 
+# FP64 lane operations per node update of the 3D step (ncu counts in profiles/flops_step_d3q27.md)
+# and GB300's FP64 pipe rate: 2 lane operations per SM per clock.
+FP64_OPS_PER_NODE_3D = 1065.8
+FP64_LANE_OPS_PER_SM_CLK = 2
+
+
+def fp64_alu_roofline(mlups: float, sms: int = 152, clock_ghz: float = 2.07):
+    peak = sms * FP64_LANE_OPS_PER_SM_CLK * clock_ghz              # G lane-ops / s
+    achieved = mlups * 1e6 * FP64_OPS_PER_NODE_3D / 1e9
+    return {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1),
+            "unit": "G FP64 lane-ops/s", "frac": round(achieved / peak, 4),
+            "peak_kind": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz"}
+
+
 def measure_forms(L, torch, stream, args):
     """MLUPS and HBM fraction of the other lattice / precision forms on the same GPU."""
     out = []
@@ -328,11 +342,14 @@ def measure_forms(L, torch, stream, args):
         s = e0.elapsed_time(e1) / 1e3 / k
         bpn = lat.info().bytes_per_node_update
         gbs = bpn * lat.n / s / 1e9
-        out.append({"lattice": "D3Q27+D3Q15" if lat_name == "d3q27" else "D2Q9+D2Q9",
-                    "precision": prec, "box": [nx, ny, nz], "mlups": round(lat.n / s / 1e6, 1),
-                    "ms_per_step": round(s * 1e3, 4), "gbs": round(gbs, 1),
-                    "hbm_frac": round(gbs / peak, 4), "steps": k,
-                    "g_attractors": "option B" if gopt else "option A"})
+        rec = {"lattice": "D3Q27+D3Q15" if lat_name == "d3q27" else "D2Q9+D2Q9",
+               "precision": prec, "box": [nx, ny, nz], "mlups": round(lat.n / s / 1e6, 1),
+               "ms_per_step": round(s * 1e3, 4), "gbs": round(gbs, 1),
+               "hbm_frac": round(gbs / peak, 4), "steps": k,
+               "g_attractors": "option B" if gopt else "option A"}
+        if lat_name == "d3q27" and prec == "fp64":
+            rec["roofline"] = fp64_alu_roofline(lat.n / s / 1e6)
+        out.append(rec)
         lat.close()
     return out
 
