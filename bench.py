@@ -189,6 +189,8 @@ def run_gpu(args):
     with torch.cuda.stream(stream):
         lat = L.Lattice(w["lattice"], w["nx"], w["ny"], w["nz"], w["Ra"], w["Pr"], w["Ma"],
                         walls=walls, precision=w["precision"], stream=stream)
+    if args.tma_rows:
+        lat.set_param("tma_rows", args.tma_rows)
     if args.block:
         bx, by = (int(v) for v in args.block.lower().split("x"))
         lat.set_param("block_x", bx)
@@ -564,6 +566,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--block", default=None, help="thread-block shape of the step, e.g. 128x1")
+    ap.add_argument("--tma-rows", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="TMA-staged 3D step with tiles of 64 x rows nodes (0 = plain step)")
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "fp16s"])
     ap.add_argument("--nx", type=int, default=None, help="override the box (profiling cases)")
     ap.add_argument("--ny", type=int, default=None)

@@ -135,7 +135,10 @@ LBM_API int lbm_set_omegas(lbm_handle h, const double* om_f, int n_f, const doub
  * moments), "adjoint_fp64" (0 or 1: arithmetic of lbm_adjoint_step's vector-Jacobian products),
  * "graph_steps" (even count of steps that lbm_step replays as one CUDA graph; 0 disables), or the
  * thread-block shape of the step launch, "block_x" (32, 64, 128 or 256) and "block_y"
- * (block_x * block_y <= 256).  Errors: LBM_EINVAL for an unknown key, a rate outside (0, 2) or a
+ * (block_x * block_y <= 256), or "tma_rows" (0 = off; 1, 2 or 4: the 3D FP32 / FP16S step stages
+ * its pull through shared memory with tensor copies in tiles of 64 x tma_rows nodes; results are
+ * bitwise those of the plain step; needs nx times the element size to be a multiple of 16 bytes,
+ * else LBM_ENOTSUP).  Errors: LBM_EINVAL for an unknown key, a rate outside (0, 2) or a
  * bad block shape. */
 LBM_API int lbm_set_param(lbm_handle h, const char* key, double value);
 LBM_API int lbm_info(lbm_handle h, lbm_info_t* out);

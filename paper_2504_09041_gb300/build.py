@@ -17,7 +17,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden"]
 SOURCES = ["api.cu", "aux.cu", "step2d.cu", "step3d_f32.cu", "step3d_f64.cu", "step3d_f16s.cu",
-           "noalloc.cu", "adjoint.cu", "batch.cu"]
+           "noalloc.cu", "adjoint.cu", "batch.cu", "tma.cu"]
 
 
 def _nvcc() -> str:

@@ -52,6 +52,8 @@ struct lbm_s {
     cudaStream_t stream = nullptr;
     int block_x = 0, block_y = 0;   // launch shape of the step kernel (0: default)
     int adjoint_fp64 = 1;           // arithmetic of the adjoint's vector-Jacobian products
+    int tma_rows = 0;               // 3D FP32/FP16S: TMA-staged step with tiles of 64 x tma_rows
+    lbm::TmaMaps tm[2];             // tensor maps of the input buffers f[c], g[c]
     // CUDA graphs of graph_steps consecutive steps (even, so the A/B parity returns), one per
     // starting parity, rebuilt whenever a launch parameter changes (gen != graph_gen)
     int graph_steps = 32;
@@ -413,6 +415,27 @@ int lbm_set_param(lbm_handle h, const char* key, double v)
         }
         return LBM_OK;
     }
+    if (k == "tma_rows") {
+        const int v_i = (int)v;
+        if (v != (double)v_i || !(v_i == 0 || v_i == 1 || v_i == 2 || v_i == 4))
+            return fail(h, LBM_EINVAL, "tma_rows must be 0 (off), 1, 2 or 4");
+        if (v_i == 0) {
+            h->tma_rows = 0;
+            return LBM_OK;
+        }
+        if (h->dim != 3 || h->prec == lbm::kF64)
+            return fail(h, LBM_ENOTSUP, "the TMA-staged step covers the 3D FP32 and FP16S forms");
+        const int eb = (int)lbm::storage_bytes(h->prec);
+        for (int c = 0; c < 2; ++c) {
+            std::string e;
+            if (!lbm::make_tma_map(&h->tm[c].f, h->f[c], eb, h->nx, h->ny, h->nz, 27, v_i, &e) ||
+                !lbm::make_tma_map(&h->tm[c].g, h->g[c], eb, h->nx, h->ny, h->nz, 15, v_i, &e))
+                return fail(h, LBM_ENOTSUP, "%s", e.c_str());
+            h->tm[c].ty = v_i;
+        }
+        h->tma_rows = v_i;
+        return LBM_OK;
+    }
     if (k == "g_attractors") {
         if (!(v == 0.0 || v == 1.0)) return fail(h, LBM_EINVAL, "g_attractors must be 0 (option A) or 1 (option B)");
         h->hc.gopt = (int)v;
@@ -488,7 +511,8 @@ static int build_graph(lbm_s* h, int par)
     int c = par;
     for (int t = 0; t < h->graph_steps && e == cudaSuccess; ++t) {
         e = lbm::launch_step(h->dim, h->prec, h->f[c], h->g[c], h->f[1 - c], h->g[1 - c], h->geo, h->hc,
-                             h->status, dim3(h->block_x, h->block_y, 1), h->capture_stream);
+                             h->status, dim3(h->block_x, h->block_y, 1), h->capture_stream,
+                             h->tma_rows ? &h->tm[c] : nullptr);
         c = 1 - c;
     }
     const cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
@@ -522,7 +546,7 @@ int lbm_step(lbm_handle h, long n)
         const int c = h->cur;
         LBM_CK(h, lbm::launch_step(h->dim, h->prec, h->f[c], h->g[c], h->f[1 - c], h->g[1 - c],
                                    h->geo, h->hc, h->status, dim3(h->block_x, h->block_y, 1),
-                                   h->stream));
+                                   h->stream, h->tma_rows ? &h->tm[c] : nullptr));
         h->cur = 1 - c;
         ++h->steps;
     }

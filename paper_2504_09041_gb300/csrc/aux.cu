@@ -12,9 +12,11 @@ size_t storage_bytes(int prec)
 
 cudaError_t launch_step(int dim, int prec, const void* fin, const void* gin, void* fout, void* gout,
                         const Geometry& geo, const HostCoeffs& hc, unsigned* status, dim3 block,
-                        cudaStream_t st)
+                        cudaStream_t st, const TmaMaps* tma)
 {
     if (dim == 2) return launch_step_d2q9(prec, fin, gin, fout, gout, geo, hc, status, block, st);
+    if (tma && prec == kF32) return launch_step_d3q27_tma_f32(*tma, fin, gin, fout, gout, geo, hc, status, st);
+    if (tma && prec == kF16S) return launch_step_d3q27_tma_f16s(*tma, fin, gin, fout, gout, geo, hc, status, st);
     switch (prec) {
     case kF64: return launch_step_d3q27_f64(fin, gin, fout, gout, geo, hc, status, block, st);
     case kF32: return launch_step_d3q27_f32(fin, gin, fout, gout, geo, hc, status, block, st);

@@ -1,6 +1,7 @@
 // kernels.h -- host-side launchers of the CUDA kernels (internal to liblbm.so).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -35,10 +36,29 @@ int plan_box(int lattice, int nx, int ny, int nz, double Ra, double Pr, double M
 // The process-wide device allocator hooks of lbm_set_allocator.
 void current_allocator(lbm_alloc_fn* a, lbm_free_fn* f, void** ctx);
 
+// Tensor maps of the input buffers of a TMA-staged 3D step (step_d3q27_tma.cuh) and its tile
+// height (1, 2 or 4 rows of 64 nodes).
+struct TmaMaps {
+    CUtensorMap f, g;
+    int ty;
+};
+// Encode the 4D map (x, y, z, plane) of one population buffer with boxes of (64 + 32 / elem_bytes)
+// x ty x 1 x 1 elements.
+// Fails (returns false, with a message) when the x stride is not a multiple of 16 bytes.
+bool make_tma_map(CUtensorMap* out, void* base, int elem_bytes, int nx, int ny, int nz, int planes,
+                  int ty, std::string* err);
+
 // block: thread-block shape of the step launch (x-major); block.x == 0 selects the default.
+// tma: tensor maps of fin / gin for the TMA-staged 3D step (FP32 and FP16S), or nullptr.
 cudaError_t launch_step(int dim, int prec, const void* fin, const void* gin, void* fout, void* gout,
                         const Geometry& geo, const HostCoeffs& hc, unsigned* status, dim3 block,
-                        cudaStream_t st);
+                        cudaStream_t st, const TmaMaps* tma = nullptr);
+cudaError_t launch_step_d3q27_tma_f32(const TmaMaps& tm, const void* fin, const void* gin, void* fout,
+                                      void* gout, const Geometry& geo, const HostCoeffs& hc,
+                                      unsigned* status, cudaStream_t st);
+cudaError_t launch_step_d3q27_tma_f16s(const TmaMaps& tm, const void* fin, const void* gin, void* fout,
+                                       void* gout, const Geometry& geo, const HostCoeffs& hc,
+                                       unsigned* status, cudaStream_t st);
 cudaError_t launch_step_d2q9(int prec, const void* fin, const void* gin, void* fout, void* gout,
                              const Geometry& geo, const HostCoeffs& hc, unsigned* status,
                              dim3 block, cudaStream_t st);

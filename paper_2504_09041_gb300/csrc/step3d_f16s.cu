@@ -1,7 +1,9 @@
 // step3d_f16s.cu -- the fused D3Q27 flow + D3Q15 energy step with StoreF16S storage (one
 // translation unit per storage type so that the three heavy instantiations compile in parallel).
+#include <algorithm>
+
 #include "kernels.h"
-#include "step_d3q27.cuh"
+#include "step_d3q27_tma.cuh"
 
 namespace lbm {
 
@@ -21,6 +23,45 @@ cudaError_t launch_step_d3q27_f16s(const void* fin, const void* gin, void* fout,
         step_d3q27_kernel<S, size_t><<<grid_shape(geo, b), b, 0, st>>>(
             (const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo, c, status);
     return cudaGetLastError();
+}
+
+template <int TY>
+static cudaError_t launch_tma_f16s(const TmaMaps& tm, const void* fin, const void* gin, void* fout,
+                                  void* gout, const Geometry& geo, const HostCoeffs& hc,
+                                  unsigned* status, cudaStream_t st)
+{
+    using S = StoreF16S;
+    using T = typename S::T;
+    using R = typename S::R;
+    using L = TmaLayout<T, TY>;
+    const auto c = make_coeffs<R, 27, 15>(hc);
+    const int tiles_x = (geo.nx + kTmaTX - 1) / kTmaTX, tiles_y = (geo.ny + TY - 1) / TY;
+    const int n_tiles = tiles_x * tiles_y * geo.nz;
+    const dim3 block(kTmaTX * TY + 32, 1, 1);   // TY rows of consumers and one producer warp
+    auto kern = index32(geo, 27) ? step_d3q27_tma_kernel<S, unsigned, TY> : step_d3q27_tma_kernel<S, size_t, TY>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTmaTX * TY + 32, L::kSmemBytes)) != cudaSuccess)
+        return e;
+    const int grid = std::max(1, std::min(n_tiles, sms * std::max(1, per_sm)));
+    kern<<<grid, block, L::kSmemBytes, st>>>(tm.f, tm.g, (const T*)fin, (const T*)gin, (T*)fout, (T*)gout,
+                                            geo, c, status, tiles_x, tiles_y, n_tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_d3q27_tma_f16s(const TmaMaps& tm, const void* fin, const void* gin, void* fout,
+                                      void* gout, const Geometry& geo, const HostCoeffs& hc,
+                                      unsigned* status, cudaStream_t st)
+{
+    switch (tm.ty) {
+    case 1: return launch_tma_f16s<1>(tm, fin, gin, fout, gout, geo, hc, status, st);
+    case 2: return launch_tma_f16s<2>(tm, fin, gin, fout, gout, geo, hc, status, st);
+    case 4: return launch_tma_f16s<4>(tm, fin, gin, fout, gout, geo, hc, status, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace lbm

@@ -373,6 +373,16 @@ __device__ __forceinline__ void collide_g_d3q15(R g[15], R T, R ux, R uy, R uz, 
     g[14] = e * (D0 - D1_);
 }
 
+// Macroscopic fields, both collisions and the store of one node whose pulled deviations are in
+// f (flow) and g (energy); i is the node's linear index.
+template <class S, class Idx>
+__device__ __forceinline__ void collide_store_d3q27(typename S::R f[27], typename S::R g[15],
+                                                    typename S::T* __restrict__ fout,
+                                                    typename S::T* __restrict__ gout,
+                                                    const Geometry& geo,
+                                                    const Coeffs3D<typename S::R>& c,
+                                                    unsigned* status, int i);
+
 template <class S, class Idx>
 __device__ __forceinline__ void node_step_d3q27(const typename S::T* __restrict__ fin,
                                                 const typename S::T* __restrict__ gin,
@@ -400,7 +410,18 @@ __device__ __forceinline__ void node_step_d3q27(const typename S::T* __restrict_
         const NodeWalls<R> w = node_walls<R>(geo, x, y, z, 3);
         pull_d3q27_d3q15<S, Idx>(fin, gin, geo, w, i, c.T_ref, f, g);
     }
+    collide_store_d3q27<S, Idx>(f, g, fout, gout, geo, c, status, i);
+}
 
+template <class S, class Idx>
+__device__ __forceinline__ void collide_store_d3q27(typename S::R f[27], typename S::R g[15],
+                                                    typename S::T* __restrict__ fout,
+                                                    typename S::T* __restrict__ gout,
+                                                    const Geometry& geo,
+                                                    const Coeffs3D<typename S::R>& c,
+                                                    unsigned* status, int i)
+{
+    using R = typename S::R;
     // rho = 1 + sum delta, rho u = sum delta e + F/2, T = T_o + sum gamma
     R dT = g[0];
 #pragma unroll
