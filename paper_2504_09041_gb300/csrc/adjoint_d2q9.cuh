@@ -291,70 +291,103 @@ __device__ __forceinline__ void relax_g_d2q9_vjp(const Coeffs2D<RT>& c, const RT
     nb[2][2] = n22b;
 }
 
-// Vector-Jacobian product of the node collision: pulled deviations (pf, pg), adjoints of the
-// post-collision deviations (lf, lg) -> adjoints of the pulled deviations (mf, mg).
+// Forward values of one node's collision that its vector-Jacobian product needs, computed in the
+// register type RF of the forward step (FP32 for FP32 / FP16S states: the same arithmetic the
+// forward step applied) and handed to the reverse in RT.
 template <class RT>
-__device__ __forceinline__ void collide_vjp_d2q9(const RT pf[9], const RT pg[9], const RT lf[9],
-                                                 const RT lg[9], const Coeffs2D<RT>& c, RT mf[9],
-                                                 RT mg[9])
+struct CollideTape {
+    RT drho, jx, jy, irho, ux, uy, Fx, Fy, T;
+    RT gX[3][3], gN[3][3], gT[3][3], gY[3][3];   // energy: line inputs, central, relaxed, inverse
+    RT fX[3][3], fD[3][3], fT[3][3], fY[3][3];   // flow (deviations): the same four stages
+};
+
+template <class RF, class RT>
+__device__ __forceinline__ void collide_forward_tape(const RF pf[9], const RF pg[9],
+                                                     const Coeffs2D<RF>& c, CollideTape<RT>& tp)
 {
-    const RT half = RT(0.5);
-    // forward recompute: macroscopic fields
-    RT dT = 0, drho = 0, jx = 0, jy = 0;
+    const RF half = RF(0.5);
+    RF dT = 0, drho = 0, jx = 0, jy = 0;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
         dT += pg[a];
         drho += pf[a];
-        jx += pf[a] * RT(e9(a, 0));
-        jy += pf[a] * RT(e9(a, 1));
+        jx += pf[a] * RF(e9(a, 0));
+        jy += pf[a] * RF(e9(a, 1));
     }
-    const RT Fb = c.gbeta * dT;
-    const RT Fx = c.gaxis == 0 ? Fb : RT(0), Fy = c.gaxis == 1 ? Fb : RT(0);
-    const RT rho = RT(1) + drho, irho = RT(1) / rho;
-    const RT ux = (jx + half * Fx) * irho, uy = (jy + half * Fy) * irho;
-    const RT T = c.T_ref + dT;
-
-    RT uxb = 0, uyb = 0, drhob = 0, irhob = 0, Fxb = 0, Fyb = 0, dTb = 0;
-
-    // energy chain: g = w T_ref + gamma -> sweeps -> relax -> inverse sweeps
-    {
-        RT gin[9];
+    const RF Fb = c.gbeta * dT;
+    const RF Fx = c.gaxis == 0 ? Fb : RF(0), Fy = c.gaxis == 1 ? Fb : RF(0);
+    const RF rho = RF(1) + drho, irho = RF(1) / rho;
+    const RF ux = (jx + half * Fx) * irho, uy = (jy + half * Fy) * irho;
+    const RF T = c.T_ref + dT;
+    tp.drho = RT(drho); tp.jx = RT(jx); tp.jy = RT(jy); tp.irho = RT(irho);
+    tp.ux = RT(ux); tp.uy = RT(uy); tp.Fx = RT(Fx); tp.Fy = RT(Fy); tp.T = RT(T);
+    auto keep = [](const RF in[3][3], RT out[3][3]) {
 #pragma unroll
-        for (int a = 0; a < 9; ++a) gin[a] = pg[a] + RT(w9(a)) * c.T_ref;
-        RT X[3][3], N[3][3], Tm[3][3], Y[3][3];
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) out[j][a] = RT(in[j][a]);
+    };
+    {
+        RF gin[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) gin[a] = pg[a] + RF(w9(a)) * c.T_ref;
+        RF X[3][3], N[3][3], Tm[3][3], Y[3][3];
         sweeps_fwd(gin, X, N, ux, uy);
+        keep(X, tp.gX);
+        keep(N, tp.gN);
 #pragma unroll
         for (int j = 0; j < 3; ++j)
 #pragma unroll
             for (int a = 0; a < 3; ++a) Tm[j][a] = N[j][a];
         relax_g_d2q9(Tm, T, c);
-        RT Tpost[3][3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) Tpost[j][a] = Tm[j][a];
+        keep(Tm, tp.gT);
         unsweeps_fwd(Tm, Y, uy);
-        RT Tb[3][3], Nb[3][3];
-        unsweeps_vjp(Tm, Y, lg, ux, uy, Tb, uxb, uyb);
-        RT Tfb = 0;
-        relax_g_d2q9_vjp(c, Tpost, T, Tb, Nb, Tfb);
-        dTb += Tfb;
-        sweeps_vjp(X, N, Nb, ux, uy, mg, uxb, uyb);
+        keep(Y, tp.gY);
     }
-    // flow chain on deviations
     {
-        RT X[3][3], D[3][3], Tm[3][3], Y[3][3];
+        RF X[3][3], D[3][3], Tm[3][3], Y[3][3];
         sweeps_fwd(pf, X, D, ux, uy);
+        keep(X, tp.fX);
+        keep(D, tp.fD);
 #pragma unroll
         for (int j = 0; j < 3; ++j)
 #pragma unroll
             for (int a = 0; a < 3; ++a) Tm[j][a] = D[j][a];
         relax_f_d2q9(Tm, drho, irho, ux, uy, Fx, Fy, c);
+        keep(Tm, tp.fT);
         unsweeps_fwd(Tm, Y, uy);
+        keep(Y, tp.fY);
+    }
+}
+
+// Vector-Jacobian product of the node collision at the forward values tp: adjoints of the
+// post-collision deviations (lf, lg) -> adjoints of the pulled deviations (mf, mg), in RT.
+template <class RT>
+__device__ __forceinline__ void collide_vjp_d2q9(const CollideTape<RT>& tp, const RT lf[9],
+                                                 const RT lg[9], const Coeffs2D<RT>& c, RT mf[9],
+                                                 RT mg[9])
+{
+    const RT half = RT(0.5);
+    const RT drho = tp.drho, jx = tp.jx, jy = tp.jy, irho = tp.irho, ux = tp.ux, uy = tp.uy;
+    const RT Fx = tp.Fx, Fy = tp.Fy, T = tp.T;
+
+    RT uxb = 0, uyb = 0, drhob = 0, irhob = 0, Fxb = 0, Fyb = 0, dTb = 0;
+
+    // energy chain: g = w T_ref + gamma -> sweeps -> relax -> inverse sweeps
+    {
+        RT Tb[3][3], Nb[3][3];
+        unsweeps_vjp(tp.gT, tp.gY, lg, ux, uy, Tb, uxb, uyb);
+        RT Tfb = 0;
+        relax_g_d2q9_vjp(c, tp.gT, T, Tb, Nb, Tfb);
+        dTb += Tfb;
+        sweeps_vjp(tp.gX, tp.gN, Nb, ux, uy, mg, uxb, uyb);
+    }
+    // flow chain on deviations
+    {
         RT Tb[3][3], Db[3][3];
-        unsweeps_vjp(Tm, Y, lf, ux, uy, Tb, uxb, uyb);
-        relax_f_d2q9_vjp(D, drho, irho, ux, uy, Fx, Fy, c, Tb, Db, drhob, irhob, uxb, uyb, Fxb, Fyb);
-        sweeps_vjp(X, D, Db, ux, uy, mf, uxb, uyb);
+        unsweeps_vjp(tp.fT, tp.fY, lf, ux, uy, Tb, uxb, uyb);
+        relax_f_d2q9_vjp(tp.fD, drho, irho, ux, uy, Fx, Fy, c, Tb, Db, drhob, irhob, uxb, uyb, Fxb, Fyb);
+        sweeps_vjp(tp.fX, tp.fD, Db, ux, uy, mf, uxb, uyb);
     }
     // macroscopic fields: u = (j + F/2) irho, irho = 1 / (1 + drho), F = g beta dT along gravity
     const RT jxb = uxb * irho, jyb = uyb * irho;
@@ -422,14 +455,10 @@ __global__ void __launch_bounds__(128)
     // forward pull of p_k from s_{k-1}
     R fr[9], gr[9];
     pull_d2q9<S, size_t>(f_prev, g_prev, geo, w, i, cr.T_ref, fr, gr);
-    RT pf[9], pg[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        pf[a] = (RT)fr[a];
-        pg[a] = (RT)gr[a];
-    }
+    CollideTape<RT> tape;
+    collide_forward_tape(fr, gr, cr, tape);
     RT mf[9], mg[9];
-    collide_vjp_d2q9(pf, pg, lf, lg, c, mf, mg);
+    collide_vjp_d2q9(tape, lf, lg, c, mf, mg);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
         mu_out[(size_t)a * n + i] = mf[a];
