@@ -16,10 +16,13 @@
     1e-4 of its Cauchy-Schwarz scale |grad| |v| (the relative error of the gradient vector).
   * The FP32 adjoint arithmetic (adjoint_fp64 = 0) against the FP64 default on that workload.
   * The torch.autograd.Function wrapper returns the same gradient.
+  * The oracle adjoint: directional derivatives of the generic-form oracle by complex step, exact
+    to rounding, against the GPU gradient (FP64 states) within 1e-8 relative, options A and B.
 """
 import numpy as np
 import pytest
 
+from oracle import generic2d as GEN
 from oracle import oracle as O
 from tests import synth
 
@@ -85,6 +88,38 @@ def test_adjoint_option_b_matches_oracle_finite_differences():
     scale = np.abs(fd).max()
     assert scale > 0
     np.testing.assert_allclose(grad, fd, rtol=0, atol=1e-6 * scale)
+
+
+@pytest.mark.parametrize("g_option", [0, 1])
+def test_adjoint_matches_the_complex_step_oracle(g_option):
+    """grad . v from lbm_adjoint_step against Im(J(T_w + i h v)) / h of the generic-form oracle."""
+    nx, ny, steps, Ra = 24, 20, 150, 1e5
+    bc = O.cavity_bc(2)
+    prof = synth.sine_profile(7, ny)
+    ora = O.Oracle(2, nx, ny, bc=bc, Ra=Ra, Pr=0.71, Ma=0.1)
+    om_g = ora.om_g.copy()
+    if g_option:
+        om_g[3:6] = (1.3, 0.8, 1.6)    # second-order energy rates away from 1: options differ
+    f0, g0 = ora.get_state()
+
+    lat = L.Lattice("d2q9", nx, ny, Ra=Ra, walls=L.Walls.cavity(2), precision="fp64")
+    lat.set_omegas(None, om_g)
+    lat.set_param("g_attractors", g_option)
+    lat.set_wall_profile(HOT, prof)
+    J, grad = lat.adjoint(steps, COLD, HOT)
+
+    rng = np.random.default_rng(17)
+    dirs = [rng.uniform(-1, 1, ny), np.eye(ny)[3], np.eye(ny)[ny // 2]]
+    h = 1e-20
+    for v in dirs:
+        gen = GEN.Generic2D(nx, ny, bc.face, bc.T_wall, bc.T_ref, ora.gbeta, bc.gravity_axis, ora.om_f,
+                            om_g, g_option, dtype=np.complex128)
+        gen.set_state(f0, g0)
+        gen.set_wall_profile(HOT, prof + 1j * h * v)
+        gen.step(steps)
+        Jc = gen.nusselt_mean(COLD, ora.L, ora.dT)
+        assert Jc.real == pytest.approx(J, abs=1e-11)
+        assert grad @ v == pytest.approx(Jc.imag / h, rel=1e-8)
 
 
 def test_adjoint_handles_uneven_segments_and_fp32():
