@@ -301,6 +301,7 @@ def run_gpu(args):
         line["batched"] = batched
     if adjoint:
         line["adjoint"] = adjoint
+    line["paper_context"] = PAPER_CONTEXT
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     return line
@@ -518,10 +519,48 @@ def oracle_sample(seconds: float):
     return nodes / t_sum / 1e6, O.threads(), desc
 
 
+def oracle_single_thread(seconds: float):
+    """The same slab sample on one host thread (a child process with OMP_NUM_THREADS=1)."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "m, c, d = bench.oracle_sample(%r); print(json.dumps([m, c]))" % (ROOT, seconds))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        return None
+    m, c = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": round(m, 4), "unit": "MLUPS", "cores": c}
+
+
+def oracle_cavity_64():
+    """The 64^2 differentially heated cavity (Ra 1e4, Pr 0.71, Ma 0.1) run to 20000 steps by the
+    oracle on all host threads, with its hot-wall Nusselt number beside Table con2's 2.2431."""
+    from oracle import oracle as O
+    ora = O.Oracle(2, 64, 64, 1, bc=O.cavity_bc(2), Ra=1e4, Pr=0.71, Ma=0.1)
+    t0 = time.perf_counter()
+    ora.step(20000)
+    t = time.perf_counter() - t0
+    return {"seconds": round(t, 2), "mlups": round(64 * 64 * 20000 / t / 1e6, 3),
+            "nu_hot_mean": round(ora.nusselt(0)[0], 5), "table_con2_512": 2.2431,
+            "cores": O.threads()}
+
+
+# The paper's only timing (context, not a target): 128^3 D3Q27 + D3Q15 at Ra 1e8, 5e6 steps in
+# 30.7 h on 512 CPU cores (C++ + MPI), i.e. 128^3 * 5e6 / (30.7 * 3600 s) node updates per second.
+PAPER_CONTEXT = {"value": round(128 ** 3 * 5e6 / (30.7 * 3600) / 1e6, 1), "unit": "MLUPS",
+                 "hardware": "512 CPU cores (INCLINE cluster), C++ with MPI",
+                 "workload": "3D D3Q27 flow + D3Q15 energy, 128^3, Ra 1e8",
+                 "precision": "not stated", "source": "Sec. 6.2 (run time) and Sec. 7"}
+
+
 def cpu_baseline(seconds: float = 15.0):
     mlups, cores, desc = oracle_sample(seconds)
-    return {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": desc}
+    out = {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+           "sample": desc}
+    single = oracle_single_thread(min(5.0, seconds))
+    if single:
+        out["single_thread"] = single
+    out["cavity_64x64_20000_steps"] = oracle_cavity_64()
+    return out
 
 
 def run_reference(args):
