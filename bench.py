@@ -183,9 +183,12 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
     w = WORKLOAD
-    walls = L.Walls.cavity(3)
+    three_d = w["lattice"] == "d3q27"
+    # 3D: the side-heated cubic cavity; 2D: the Rayleigh-Benard box (periodic x, hot bottom)
+    walls = L.Walls.cavity(3) if three_d else L.Walls.rayleigh_benard()
     walls.seed = 1000 + rank        # each rank: its own ensemble member
     walls.perturb = 1e-3
+    hot, cold = (0, 1) if three_d else (2, 3)
     with torch.cuda.stream(stream):
         lat = L.Lattice(w["lattice"], w["nx"], w["ny"], w["nz"], w["Ra"], w["Pr"], w["Ma"],
                         walls=walls, precision=w["precision"], stream=stream)
@@ -204,7 +207,7 @@ def run_gpu(args):
     with ClockSampler(local) as clocks:
         # warm-up (also gives the clock sampler time to start)
         lat.step(args.warmup)
-        lat.nusselt(0)
+        lat.nusselt(hot)
         lat.sync()
         barrier(world)
         torch.cuda.synchronize()
@@ -212,8 +215,8 @@ def run_gpu(args):
         ev[0].record(stream)
         lat.step(args.steps)
         ev[1].record(stream)
-        nu_hot = L.lbm_nusselt(lat.h, 0)
-        nu_cold = L.lbm_nusselt(lat.h, 1)
+        nu_hot = L.lbm_nusselt(lat.h, hot)
+        nu_cold = L.lbm_nusselt(lat.h, cold)
         ev[2].record(stream)
         torch.cuda.synchronize()
         clocks.mark(t_start, datetime.now())
@@ -234,8 +237,8 @@ def run_gpu(args):
     t0 = time.perf_counter()
     L.lbm_set_state(lat.h, state_host.numpy())
     L.lbm_step(lat.h, args.steps)
-    L.lbm_nusselt(lat.h, 0)
-    L.lbm_nusselt(lat.h, 1)
+    L.lbm_nusselt(lat.h, hot)
+    L.lbm_nusselt(lat.h, cold)
     L.lbm_fields(lat.h, None, None, None, None, T_host.data_ptr(), 0)
     torch.cuda.synchronize()
     t_e2e = reduce_max(time.perf_counter() - t0, world)
@@ -258,7 +261,10 @@ def run_gpu(args):
     step_s = t_steps / args.steps
     achieved = bpn * n / step_s / 1e9
     peak, peak_kind = hbm_peak()
-    traffic = committed_traffic()
+    # the committed ncu traffic describes the 256^3 FP32 step only
+    traffic = (committed_traffic() if three_d and w["precision"] == "fp32"
+               and (w["nx"], w["ny"], w["nz"]) == (256, 256, 256) else None)
+    state_gb = bpn / 2 * n / 1e9
     e2e = job_mlups(n, args.steps, world, t_e2e)
     line = {
         "metric": METRIC,
@@ -273,17 +279,24 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "fp16s": "f16 storage, f32 arithmetic"}[w["precision"]],
         "data": "synthetic (seeded initial temperature perturbation +-1e-3 of the cavity at rest)",
-        "config": {"workload": "3D differentially heated cubic cavity, D3Q27 flow + D3Q15 energy, "
-                               "FP32 populations, FP64 Nusselt reduction",
+        "config": {"workload": ("3D differentially heated cubic cavity, D3Q27 flow + D3Q15 energy, "
+                                f"{w['precision'].upper()} populations, FP64 Nusselt reduction")
+                   if three_d else
+                               ("2D Rayleigh-Benard box, D2Q9 flow + D2Q9 energy, "
+                                f"{w['precision'].upper()} populations, FP64 Nusselt reduction"),
                    "nx": w["nx"], "ny": w["ny"], "nz": w["nz"], "Ra": w["Ra"], "Pr": w["Pr"],
                    "Ma": w["Ma"], "nodes_per_gpu": n, "bytes_per_node_update": bpn,
                    "nusselt_every": args.steps,
-                   "l2": "inputs larger than L2 (2.8 GB read and 2.8 GB written per step)",
+                   "l2": (f"inputs larger than L2 ({state_gb:.2f} GB read and {state_gb:.2f} GB "
+                          "written per step)") if state_gb > 0.129 else
+                         f"inputs fit in L2 ({state_gb * 1e3:.0f} MB per step): not an HBM figure",
                    "parallelism": "independent cavity per GPU (ensemble member)" if world > 1
                    else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "peak_kind": peak_kind, "kernel": "step_d3q27_kernel<StoreF32>",
+                     "peak_kind": peak_kind,
+                     "kernel": ("step_d3q27_kernel" if three_d else "step_d2q9_kernel")
+                     + "<Store" + {"fp32": "F32", "fp64": "F64", "fp16s": "F16S"}[w["precision"]] + ">",
                      "launch_ms": round(step_s * 1e3, 4), "traffic_unit": "bytes per launch",
                      "block": [info.block_x, info.block_y]},
         "e2e": {"value": round(e2e, 2), "unit": "MLUPS",
@@ -307,15 +320,15 @@ def run_gpu(args):
     return line
 
 
-# FP64 lane operations per node update of the 3D step (ncu counts in profiles/flops_step_d3q27.md)
-# and GB300's FP64 pipe rate: 2 lane operations per SM per clock.
-FP64_OPS_PER_NODE_3D = 1065.8
+# FP64 lane operations per node update of the FP64 steps (ncu counts in
+# profiles/flops_step_d3q27.md) and GB300's FP64 pipe rate: 2 lane operations per SM per clock.
+FP64_OPS_PER_NODE = {"d3q27": 1065.8, "d2q9": 340.6}
 FP64_LANE_OPS_PER_SM_CLK = 2
 
 
-def fp64_alu_roofline(mlups: float, sms: int = 152, clock_ghz: float = 2.07):
+def fp64_alu_roofline(mlups: float, lattice: str = "d3q27", sms: int = 152, clock_ghz: float = 2.07):
     peak = sms * FP64_LANE_OPS_PER_SM_CLK * clock_ghz              # G lane-ops / s
-    achieved = mlups * 1e6 * FP64_OPS_PER_NODE_3D / 1e9
+    achieved = mlups * 1e6 * FP64_OPS_PER_NODE[lattice] / 1e9
     return {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1),
             "unit": "G FP64 lane-ops/s", "frac": round(achieved / peak, 4),
             "peak_kind": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz"}
@@ -350,8 +363,8 @@ def measure_forms(L, torch, stream, args):
                "ms_per_step": round(s * 1e3, 4), "gbs": round(gbs, 1),
                "hbm_frac": round(gbs / peak, 4), "steps": k,
                "g_attractors": "option B" if gopt else "option A"}
-        if lat_name == "d3q27" and prec == "fp64":
-            rec["roofline"] = fp64_alu_roofline(lat.n / s / 1e6)
+        if prec == "fp64":
+            rec["roofline"] = fp64_alu_roofline(lat.n / s / 1e6, lat_name)
         out.append(rec)
         lat.close()
     return out
@@ -608,6 +621,8 @@ def main(argv=None):
     ap.add_argument("--tma-rows", type=int, default=0, choices=[0, 1, 2, 4],
                     help="TMA-staged 3D step with tiles of 64 x rows nodes (0 = plain step)")
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "fp16s"])
+    ap.add_argument("--lattice", default=None, choices=["d3q27", "d2q9"],
+                    help="main workload: the 3D cavity (default) or the 2D Rayleigh-Benard box")
     ap.add_argument("--nx", type=int, default=None, help="override the box (profiling cases)")
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)
@@ -616,6 +631,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.lattice == "d2q9":
+        WORKLOAD.update(lattice="d2q9", nx=1024, ny=512, nz=1, Ra=1e8)
     for k in ("nx", "ny", "nz", "precision"):
         if getattr(args, k) is not None:
             WORKLOAD[k] = getattr(args, k)
