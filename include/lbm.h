@@ -85,6 +85,7 @@ typedef struct {
     int block_x, block_y;       /* thread-block shape of the step launch */
     int graph_steps;            /* steps per CUDA graph replayed by lbm_step (0: plain launches) */
     int g_attractors;           /* energy attractors of orders 3-4: 0 = option A, 1 = option B */
+    int fp16_stochastic;        /* LBM_FP16S: 1 = stochastic rounding of the stored deviations */
 } lbm_info_t;
 
 /*
@@ -132,7 +133,9 @@ LBM_API int lbm_set_omegas(lbm_handle h, const double* om_f, int n_f, const doub
  * "g_attractors" (0: option A, Eqs. MvT2D / g-attractorsD3Q15optionA, the default and the paper's
  * choice; 1: option B, the renormalized energy attractors of orders 3-4 of Eq. MvT2DoptionB and
  * its D3Q15 counterpart in Sec. 5.3, with D-hat' = eta~ / T from the post-collision second
- * moments), "adjoint_fp64" (0 or 1: arithmetic of lbm_adjoint_step's vector-Jacobian products),
+ * moments), "fp16_stochastic" (LBM_FP16S storage: 1, the default, rounds each stored deviation
+ * stochastically, up or down with probabilities that make the rounding unbiased, so that updates
+ * smaller than half an FP16 step accumulate in expectation; 0 rounds to nearest), "adjoint_fp64" (0 or 1: arithmetic of lbm_adjoint_step's vector-Jacobian products),
  * "graph_steps" (even count of steps that lbm_step replays as one CUDA graph; 0 disables), or the
  * thread-block shape of the step launch, "block_x" (32, 64, 128 or 256) and "block_y"
  * (block_x * block_y <= 256), or "tma_rows" (0 = off; 1, 2 or 4: the 3D FP32 / FP16S step stages

@@ -266,6 +266,7 @@ int plan_box(int lattice, int nx, int ny, int nz, double Ra, double Pr, double M
     hc.gbeta = P->U * P->U / (P->L * P->dT);
     hc.T_ref = bc->T_ref;
     hc.gaxis = bc->gravity_axis;
+    hc.fp16_sr = 1;
     const double om_nu = 1.0 / (3.0 * P->nu + 0.5);
     const double om_alpha = 1.0 / (3.0 * P->alpha + 0.5);
     // App. A, B, C: shear / diffusivity rates from nu / alpha, bulk and every free rate 1
@@ -436,6 +437,11 @@ int lbm_set_param(lbm_handle h, const char* key, double v)
         h->tma_rows = v_i;
         return LBM_OK;
     }
+    if (k == "fp16_stochastic") {
+        if (!(v == 0.0 || v == 1.0)) return fail(h, LBM_EINVAL, "fp16_stochastic must be 0 or 1");
+        h->hc.fp16_sr = (int)v;
+        return LBM_OK;
+    }
     if (k == "g_attractors") {
         if (!(v == 0.0 || v == 1.0)) return fail(h, LBM_EINVAL, "g_attractors must be 0 (option A) or 1 (option B)");
         h->hc.gopt = (int)v;
@@ -494,6 +500,7 @@ int lbm_info(lbm_handle h, lbm_info_t* o)
     o->block_y = (int)b.y;
     o->graph_steps = h->graph_steps;
     o->g_attractors = h->hc.gopt;
+    o->fp16_stochastic = h->hc.fp16_sr;
     return LBM_OK;
 }
 

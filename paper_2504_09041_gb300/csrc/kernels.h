@@ -20,6 +20,7 @@ struct HostCoeffs {
     double gbeta, T_ref;
     int gaxis;
     int gopt;   // energy attractors of orders 3-4: 0 = option A, 1 = option B
+    int fp16_sr;   // F16S storage: stochastic (1) or nearest (0) rounding of stored deviations
 };
 
 size_t storage_bytes(int prec);
@@ -119,6 +120,7 @@ inline Coeffs<R, QF, QG> make_coeffs(const HostCoeffs& h)
     c.T_ref = R(h.T_ref);
     c.gaxis = h.gaxis;
     c.gopt = h.gopt;
+    c.fp16_sr = h.fp16_sr;
     return c;
 }
 

@@ -46,7 +46,37 @@ struct StoreF16S {
         return __half2float(__ldg(p + i)) * kInvScale;
     }
     __device__ static void store_dev(T* p, size_t i, R dev, R) { p[i] = __float2half_rn(dev * kScale); }
+    // Two deviations converted together with stochastic rounding: each is rounded up or down to a
+    // neighbouring FP16 value with probabilities that make the rounding unbiased, driven by the
+    // caller's random bits (Blackwell's cvt.rs).  Returns (half of d0) | (half of d1) << 16.
+    __device__ static unsigned pack_sr(R d0, R d1, unsigned rbits)
+    {
+        unsigned h2;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(h2) : "f"(d1 * kScale), "f"(d0 * kScale), "r"(rbits));
+        return h2;
+    }
 };
+
+// 32-bit integer mix (the "lowbias32" constants of C. Wellons' hash prospector): a counter-style
+// source of random bits for stochastic rounding.
+__device__ __forceinline__ unsigned mix32(unsigned x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// Random bits for the stochastic rounding of a pair of values of node i: a hash of the node, the
+// pair and both values' FP32 bits, so the rounding is reproducible and changes whenever an update
+// below half an FP16 step changes the FP32 value.
+__device__ __forceinline__ unsigned sr_bits(unsigned i, unsigned pair, float d0, float d1)
+{
+    return mix32(i * 0x9e3779b9u + pair * 0x85ebca6bu + (__float_as_uint(d0) ^ (__float_as_uint(d1) << 7)));
+}
+
 
 // Box geometry and wall description shared by every kernel.
 struct Geometry {
@@ -67,6 +97,7 @@ struct Coeffs {
     R gbeta, T_ref;
     int gaxis;    // 0, 1, 2
     int gopt;     // energy attractors of orders 3-4: 0 = option A, 1 = option B (renormalized)
+    int fp16_sr;  // F16S storage: 1 = stochastic rounding of the stored deviations, 0 = nearest
 };
 
 // Per-thread wall bookkeeping for the pull.  For an axis, "m" is a link whose source lies at
@@ -171,6 +202,31 @@ template <int N, class F>
 __device__ __forceinline__ void static_for(F&& f)
 {
     static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// Store of one node's 2q deviations (flow planes then energy planes) through F16S storage with
+// stochastic rounding: consecutive values are converted in pairs.
+template <int QF, int QG, class Idx>
+__device__ __forceinline__ void store_node_f16s_sr(__half* __restrict__ fout, __half* __restrict__ gout,
+                                                   Idx n, int i, const float* df, const float* dg)
+{
+    constexpr int Q = QF + QG;
+    static_for<(Q + 1) / 2>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        constexpr int a0 = 2 * k, a1 = 2 * k + 1;
+        // value a of the node: flow plane a, or energy plane a - QF (indices kept in range)
+        constexpr int f0 = a0 < QF ? a0 : 0, g0 = a0 < QF ? 0 : a0 - QF;
+        constexpr int f1 = a1 < QF ? a1 : 0, g1 = a1 < QF ? 0 : (a1 < Q ? a1 - QF : 0);
+        const float v0 = a0 < QF ? df[f0] : dg[g0];
+        const float v1 = a1 < Q ? (a1 < QF ? df[f1] : dg[g1]) : 0.0f;
+        const unsigned h2 = StoreF16S::pack_sr(v0, v1, sr_bits((unsigned)i, (unsigned)k, v0, v1));
+        const __half h0 = __ushort_as_half((unsigned short)(h2 & 0xffffu));
+        const __half h1 = __ushort_as_half((unsigned short)(h2 >> 16));
+        if (a0 < QF) fout[(Idx)a0 * n + i] = h0;
+        else gout[(Idx)(a0 - QF) * n + i] = h0;
+        if (a1 < QF) fout[(Idx)a1 * n + i] = h1;
+        else if (a1 < Q) gout[(Idx)(a1 - QF) * n + i] = h1;
+    });
 }
 
 // Divergence flag: bit 0 set when a node sees a non-finite or non-positive density or a

@@ -230,6 +230,17 @@ __device__ __forceinline__ void node_step_d2q9(const typename S::T* __restrict__
     relax_g_d2q9(p, T, c);
     from_central_d2q9(p, g, ux, uy);
 
+    if constexpr (std::is_same<S, StoreF16S>::value) {
+        if (c.fp16_sr) {
+            R dg[9];
+            static_for<9>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                dg[a] = g[a] - R(w9(a)) * c.T_ref;
+            });
+            store_node_f16s_sr<9, 9, Idx>(fout, gout, (Idx)geo.n, i, f, dg);
+            return;
+        }
+    }
     static_for<9>([&](auto A) {
         constexpr int a = decltype(A)::value;
         S::store_dev(fout, (Idx)a * geo.n + i, f[a], R(w9(a)));

@@ -462,6 +462,17 @@ __device__ __forceinline__ void collide_store_d3q27(typename S::R f[27], typenam
     });
     collide_g_d3q15(g, T, ux, uy, uz, c.om_g, c.gopt);
 
+    if constexpr (std::is_same<S, StoreF16S>::value) {
+        if (c.fp16_sr) {
+            R dg[15];
+            static_for<15>([&](auto B) {
+                constexpr int b = decltype(B)::value;
+                dg[b] = g[b] - R(w15(b)) * c.T_ref;
+            });
+            store_node_f16s_sr<27, 15, Idx>(fout, gout, (Idx)geo.n, i, f, dg);
+            return;
+        }
+    }
     static_for<27>([&](auto A) {
         constexpr int a = decltype(A)::value;
         S::store_dev(fout, (Idx)a * geo.n + i, f[a], R(w27(a)));

@@ -48,7 +48,8 @@ class lbm_info_t(ctypes.Structure):
                 ("om_f", ctypes.c_double * 27), ("om_g", ctypes.c_double * 15),
                 ("steps", ctypes.c_longlong), ("bytes_per_node_update", ctypes.c_double),
                 ("state_bytes", ctypes.c_size_t), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
-                ("graph_steps", ctypes.c_int), ("g_attractors", ctypes.c_int)]
+                ("graph_steps", ctypes.c_int), ("g_attractors", ctypes.c_int),
+                ("fp16_stochastic", ctypes.c_int)]
 
 
 class lbm_batch_info_t(ctypes.Structure):
