@@ -512,12 +512,14 @@ def test_rayleigh_benard_1024x512_precision_forms():
     assert nu_rn > 30.0 and u_rn < 1e-3
 
 
-@pytest.mark.parametrize("Ra,steps", [(1e5, 200000), (1e6, 250000)])
-def test_cubic_cavity_128_matches_table_compare_nu3d(Ra, steps):
+@pytest.mark.parametrize("Ra,steps,walls_rel", [(1e5, 200000, 2e-3), (1e6, 250000, 2e-3),
+                                               (1e7, 300000, 5e-3)])
+def test_cubic_cavity_128_matches_table_compare_nu3d(Ra, steps, walls_rel):
     """128^3 cubic cavity (D3Q27 flow + D3Q15 energy, FP32, Ma 0.1) at steady state against the
     hot-wall <Nu> of Table CompareNu3D (128^3, U_o = 0.01): within 1 %; hot and cold wall agree
-    within 0.2 %.  This pins the D3Q27 reading of the flow collision against the paper's own
-    3D results."""
+    within 0.2 % (0.5 % at Ra 1e7, whose thinner boundary layers take longer to settle: after
+    300k steps the hot wall is within 0.06 % of its 800k-step value).  This pins the D3Q27
+    reading of the flow collision against the paper's own 3D results."""
     import json, os
     gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
     lat = L.Lattice("d3q27", 128, 128, 128, Ra=Ra, Pr=0.71, Ma=0.1, walls=L.Walls.cavity(3),
@@ -526,9 +528,9 @@ def test_cubic_cavity_128_matches_table_compare_nu3d(Ra, steps):
     lat.sync()
     hot, cold = lat.nusselt(0)[0], lat.nusselt(1)[0]
     lat.close()
-    key = {1e5: "1e5", 1e6: "1e6"}[Ra]
+    key = {1e5: "1e5", 1e6: "1e6", 1e7: "1e7"}[Ra]
     assert hot == pytest.approx(gold["nu_mean_3d"][key], rel=0.01)
-    assert cold == pytest.approx(hot, rel=2e-3)
+    assert cold == pytest.approx(hot, rel=walls_rel)
 
 
 @pytest.mark.parametrize("dim,shape", [(2, (1, 40, 70)), (3, (9, 12, 20))])
