@@ -44,6 +44,7 @@ enum lbm_status {
     LBM_ENOMEM = 2,     /* the device allocator returned NULL */
     LBM_ECUDA = 3,      /* a CUDA call failed; lbm_last_error has the CUDA message */
     LBM_EDIVERGED = 4,  /* a node saw a non-finite or non-positive density or a non-finite T */
+    LBM_ETIMEOUT = 5,   /* a bounded device-side wait gave up (the kernel returned, no hang) */
     LBM_ENOTSUP = 6     /* valid request that this build does not support */
 };
 
@@ -222,6 +223,17 @@ LBM_API int lbm_set_state(lbm_handle h, const void* buf, size_t bytes);
 
 LBM_API const char* lbm_last_error(lbm_handle h);
 LBM_API const char* lbm_status_string(int status);
+
+/*
+ * Self-test of the bounded device waits (the TMA-staged step's mbarrier waits use the same code).
+ * One thread waits on a shared-memory mbarrier that nothing arrives on, for at most `seconds`
+ * (0 < seconds <= 10, converted with the device's clock rate), then records the timeout and
+ * returns.  The paper has no counterpart: it lets the failure path of a device wait be tested
+ * without hanging a GPU.  *timed_out receives 1 when the wait gave up (the expected outcome).
+ * Returns LBM_ETIMEOUT in that case, LBM_OK if the wait completed, LBM_EINVAL for a bad argument,
+ * LBM_ENOMEM or LBM_ECUDA on errors.  Runs on, and synchronizes, the legacy default stream.
+ */
+LBM_API int lbm_probe_bounded_wait(double seconds, int* timed_out);
 
 /*
  * Wall Nusselt reduction that allocates nothing.  The paper has no counterpart: this is the

@@ -166,6 +166,7 @@ const char* lbm_status_string(int s)
     case LBM_ENOMEM: return "out of device memory";
     case LBM_ECUDA: return "CUDA error";
     case LBM_EDIVERGED: return "simulation diverged";
+    case LBM_ETIMEOUT: return "a bounded device wait timed out";
     case LBM_ENOTSUP: return "not supported";
     }
     return "unknown status";
@@ -568,6 +569,9 @@ int lbm_sync(lbm_handle h)
     LBM_CK(h, cudaStreamSynchronize(h->stream));
     if (st) {
         LBM_CK(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+        if (st & 2u)
+            return fail(h, LBM_ETIMEOUT, "a bounded wait of the TMA-staged step gave up by step %lld",
+                        h->steps);
         return fail(h, LBM_EDIVERGED, "non-finite or non-positive density or temperature by step %lld",
                     h->steps);
     }

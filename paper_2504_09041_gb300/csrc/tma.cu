@@ -5,8 +5,20 @@
 #include <string>
 
 #include "kernels.h"
+#include "step_d3q27_tma.cuh"
 
 namespace lbm {
+
+// One thread waits, bounded, on an mbarrier that nothing arrives on.
+__global__ void probe_wait_kernel(long long limit_cycles, unsigned* result)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    const unsigned b = smem_addr(&bar);
+    mbar_init(b, 1);
+    fence_mbar_init();
+    const bool done = mbar_wait_bounded(b, 0, limit_cycles);
+    *result = done ? 0u : 2u;
+}
 
 namespace {
 
@@ -71,3 +83,27 @@ bool make_tma_map(CUtensorMap* out, void* base, int elem_bytes, int nx, int ny, 
 }
 
 }  // namespace lbm
+
+extern "C" int lbm_probe_bounded_wait(double seconds, int* timed_out)
+{
+    if (!timed_out || !(seconds > 0.0 && seconds <= 10.0)) return LBM_EINVAL;
+    int dev = 0, khz = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ECUDA;
+    }
+    unsigned* r = nullptr;
+    if (cudaMalloc(&r, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ENOMEM;
+    }
+    const long long limit = (long long)(seconds * 1e3 * (double)khz);
+    lbm::probe_wait_kernel<<<1, 1>>>(limit, r);
+    unsigned out = 1;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(&out, r, sizeof out, cudaMemcpyDeviceToHost);
+    cudaFree(r);
+    if (e != cudaSuccess) return LBM_ECUDA;
+    *timed_out = out == 2u ? 1 : 0;
+    return out == 2u ? LBM_ETIMEOUT : LBM_OK;
+}

@@ -17,7 +17,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
-LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ENOTSUP = 0, 1, 2, 3, 4, 6
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ETIMEOUT, LBM_ENOTSUP = 0, 1, 2, 3, 4, 5, 6
 LBM_D2Q9_D2Q9, LBM_D3Q27_D3Q15 = 1, 2
 LBM_FP64, LBM_FP32, LBM_FP16S = 0x000, 0x100, 0x200
 LBM_PERIODIC, LBM_WALL_ADIABATIC, LBM_WALL_FIXED_T = 0, 1, 2
@@ -97,6 +97,7 @@ def lib() -> ctypes.CDLL:
             "lbm_set_state": [H, v, s],
             "lbm_nusselt_static": [i, i, i, i, ip, dp, d, v, i, d, d, v, v],
             "lbm_adjoint_step": [H, ctypes.c_long, i, i, dp, dp, ctypes.c_long],
+            "lbm_probe_bounded_wait": [d, ip],
             "lbm_batch_create": [i, i, ip, ip, dp, dp, d, ctypes.POINTER(lbm_bc), ctypes.POINTER(H)],
             "lbm_batch_destroy": [H],
             "lbm_batch_set_stream": [H, v],
@@ -325,6 +326,16 @@ def lbm_batch_info(b) -> lbm_batch_info_t:
 
 def lbm_batch_last_error(b=None) -> str:
     return lib().lbm_batch_last_error(b).decode()
+
+
+def lbm_probe_bounded_wait(seconds: float):
+    """Self-test of the bounded device waits: returns (status, timed_out); LBM_ETIMEOUT with
+    timed_out = 1 is the expected outcome (the wait runs out and the kernel returns)."""
+    t = ctypes.c_int(-1)
+    st = lib().lbm_probe_bounded_wait(float(seconds), ctypes.byref(t))
+    if st not in (LBM_OK, LBM_ETIMEOUT):
+        raise LbmError(st, lib().lbm_status_string(st).decode())
+    return st, t.value
 
 
 def lbm_last_error(h=None) -> str:

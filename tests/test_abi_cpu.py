@@ -128,3 +128,11 @@ def test_batch_calls_reject_a_null_batch(lbm):
     assert L.lbm_batch_set_launch(None, 64, 2, 8, 32) == lbm.LBM_EINVAL
     assert L.lbm_batch_info(None, None) == lbm.LBM_EINVAL
     assert "NULL" in lbm.lbm_batch_last_error(None)
+
+
+def test_bounded_wait_probe_validates_its_limit(lbm):
+    t = ctypes.c_int(-1)
+    for bad in (0.0, -1.0, 11.0, float("nan")):
+        assert lbm.lib().lbm_probe_bounded_wait(bad, ctypes.byref(t)) == lbm.LBM_EINVAL
+    assert lbm.lib().lbm_probe_bounded_wait(0.01, None) == lbm.LBM_EINVAL
+    assert lbm.lbm_status_string(lbm.LBM_ETIMEOUT) == "a bounded device wait timed out"

@@ -68,3 +68,17 @@ def test_tma_rows_is_validated():
     ok.set_param("tma_rows", 0)
     ok.step(3)
     ok.sync()
+
+
+def test_bounded_device_wait_gives_up_and_the_context_survives():
+    """An mbarrier wait that nothing completes runs out after its limit (10 ms here), records the
+    timeout and returns: no trap, no hang.  The GPU then steps a TMA-staged box normally."""
+    import time
+    t0 = time.perf_counter()
+    st, timed_out = L.lbm_probe_bounded_wait(0.01)
+    assert st == L.LBM_ETIMEOUT and timed_out == 1
+    assert time.perf_counter() - t0 < 5.0
+    lat = L.Lattice("d3q27", 64, 16, 16, Ra=1e5, walls=L.Walls.cavity(3), precision="fp32")
+    lat.set_param("tma_rows", 2)
+    lat.step(10)
+    lat.sync()
