@@ -30,10 +30,26 @@ struct StoreF64 {
     __device__ static R load_dev(const T* p, size_t i, R shift) { return __ldg(p + i) - shift; }
     __device__ static void store_dev(T* p, size_t i, R dev, R shift) { p[i] = shift + dev; }
 };
+// Read-only loads with an L2 prefetch hint of 256 bytes: the pull reads every population plane in
+// full, so the sectors around each warp's row are always used by the neighbouring warps.
+__device__ __forceinline__ float ldg_pf256(const float* p)
+{
+    float v;
+    asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ __half ldg_pf256(const __half* p)
+{
+    unsigned short v;
+    asm("ld.global.nc.L2::256B.b16 %0, [%1];" : "=h"(v) : "l"(p));
+    return __ushort_as_half(v);
+}
+
 struct StoreF32 {
     using T = float;
     using R = float;
-    __device__ static R load_dev(const T* p, size_t i, R) { return __ldg(p + i); }
+    __device__ static R load_dev(const T* p, size_t i, R) { return ldg_pf256(p + i); }
     __device__ static void store_dev(T* p, size_t i, R dev, R) { p[i] = dev; }
 };
 struct StoreF16S {
@@ -43,7 +59,7 @@ struct StoreF16S {
     static constexpr float kInvScale = 1.0f / 1024.0f;
     __device__ static R load_dev(const T* p, size_t i, R)
     {
-        return __half2float(__ldg(p + i)) * kInvScale;
+        return __half2float(ldg_pf256(p + i)) * kInvScale;
     }
     __device__ static void store_dev(T* p, size_t i, R dev, R) { p[i] = __float2half_rn(dev * kScale); }
     // Two deviations converted together with stochastic rounding: each is rounded up or down to a
@@ -69,12 +85,22 @@ __device__ __forceinline__ unsigned mix32(unsigned x)
     return x;
 }
 
-// Random bits for the stochastic rounding of a pair of values of node i: a hash of the node, the
-// pair and both values' FP32 bits, so the rounding is reproducible and changes whenever an update
-// below half an FP16 step changes the FP32 value.
-__device__ __forceinline__ unsigned sr_bits(unsigned i, unsigned pair, float d0, float d1)
+// Seed of the stochastic rounding of node i: one full mix of the node index and the FP32 bits of two
+// of the node's new values, so the bits are reproducible and change whenever an update below half
+// an FP16 step changes the node's state.
+__device__ __forceinline__ unsigned sr_seed(unsigned i, float d0, float d1)
 {
-    return mix32(i * 0x9e3779b9u + pair * 0x85ebca6bu + (__float_as_uint(d0) ^ (__float_as_uint(d1) << 7)));
+    return mix32(i * 0x9e3779b9u + (__float_as_uint(d0) ^ (__float_as_uint(d1) << 7)));
+}
+
+// Random bits of value pair k of a node: the seed times a distinct odd constant.  Multiplication by
+// an odd constant permutes the 32-bit words, so every bit of every pair's word is uniformly
+// distributed when the seed is, which is all that unbiased rounding needs.
+template <int K>
+__device__ __forceinline__ unsigned sr_pair_bits(unsigned seed)
+{
+    constexpr unsigned mult = 0x9e3779b9u + 2u * (unsigned)K * 0x632be5abu;  // odd for every K
+    return seed * mult;
 }
 
 
@@ -211,6 +237,7 @@ __device__ __forceinline__ void store_node_f16s_sr(__half* __restrict__ fout, __
                                                    Idx n, int i, const float* df, const float* dg)
 {
     constexpr int Q = QF + QG;
+    const unsigned seed = sr_seed((unsigned)i, df[0], dg[0]);
     static_for<(Q + 1) / 2>([&](auto K) {
         constexpr int k = decltype(K)::value;
         constexpr int a0 = 2 * k, a1 = 2 * k + 1;
@@ -219,7 +246,7 @@ __device__ __forceinline__ void store_node_f16s_sr(__half* __restrict__ fout, __
         constexpr int f1 = a1 < QF ? a1 : 0, g1 = a1 < QF ? 0 : (a1 < Q ? a1 - QF : 0);
         const float v0 = a0 < QF ? df[f0] : dg[g0];
         const float v1 = a1 < Q ? (a1 < QF ? df[f1] : dg[g1]) : 0.0f;
-        const unsigned h2 = StoreF16S::pack_sr(v0, v1, sr_bits((unsigned)i, (unsigned)k, v0, v1));
+        const unsigned h2 = StoreF16S::pack_sr(v0, v1, sr_pair_bits<k>(seed));
         const __half h0 = __ushort_as_half((unsigned short)(h2 & 0xffffu));
         const __half h1 = __ushort_as_half((unsigned short)(h2 >> 16));
         if (a0 < QF) fout[(Idx)a0 * n + i] = h0;
