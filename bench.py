@@ -462,7 +462,8 @@ def run_only(args):
 
 def measure_adjoint(L, torch, stream):
     """The adjoint workload: 256^2 cavity, Ra 1e5, 2000 steps, gradient of the mean cold-wall Nu
-    with respect to the 256-node hot-wall profile; FP32 forward, FP64 adjoint.  Reports the time
+    with respect to the 256-node hot-wall profile; FP32 forward, double-float adjoint (the default),
+    with the FP64 and FP32 adjoint arithmetic timed beside it.  Reports the time
     per forward step and per adjoint step (the whole lbm_adjoint_step call, checkpointed forward,
     segment recomputation and adjoint kernels, divided by the step count)."""
     import numpy as np
@@ -484,8 +485,8 @@ def measure_adjoint(L, torch, stream):
     torch.cuda.synchronize()
     fwd = e0.elapsed_time(e1) / 1e3
     timings = {}
-    for flag in (1, 0):
-        lat.set_param("adjoint_fp64", flag)
+    for flag in (2, 1, 0):
+        lat.set_param("adjoint_arith", flag)
         lat.set_state(state0)
         lat.adjoint(50, 1, 0)          # warm-up of the adjoint path
         lat.set_state(state0)
@@ -494,7 +495,8 @@ def measure_adjoint(L, torch, stream):
         J, grad = lat.adjoint(steps, 1, 0)
         timings[flag] = (time.perf_counter() - t0, J, grad)
     lat.close()
-    adj, J, grad = timings[1]
+    adj, J, grad = timings[2]
+    adj64, _, grad64 = timings[1]
     adj32 = timings[0][0]
     return {"workload": "2D cavity 256x256, Ra 1e5, Pr 0.71, 2000 steps, dJ/dT_w of the mean "
                         "cold-wall Nu w.r.t. the 256-node hot-wall profile",
@@ -503,7 +505,11 @@ def measure_adjoint(L, torch, stream):
             "adjoint_over_forward": round(adj / fwd, 3),
             "fp32_arithmetic": {"adjoint_ms_per_step": round(adj32 / steps * 1e3, 5),
                                 "adjoint_over_forward": round(adj32 / fwd, 3)},
-            "arithmetic": "FP32 forward states, FP64 vector-Jacobian products and accumulation",
+            "fp64_arithmetic": {"adjoint_ms_per_step": round(adj64 / steps * 1e3, 5),
+                                "adjoint_over_forward": round(adj64 / fwd, 3)},
+            "max_abs_diff_vs_fp64_rel": float(np.abs(grad - grad64).max() / np.abs(grad64).max()),
+            "arithmetic": "FP32 forward states; double-float (FP32-pair, 48-bit significand) "
+                          "vector-Jacobian products and adjoint state; FP64 gradient accumulation",
             "J": J,
             "grad_norm": float(np.linalg.norm(grad)),
             "checkpoints": int(math.ceil(math.sqrt(steps)))}

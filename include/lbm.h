@@ -136,7 +136,8 @@ LBM_API int lbm_set_omegas(lbm_handle h, const double* om_f, int n_f, const doub
  * its D3Q15 counterpart in Sec. 5.3, with D-hat' = eta~ / T from the post-collision second
  * moments), "fp16_stochastic" (LBM_FP16S storage: 1, the default, rounds each stored deviation
  * stochastically, up or down with probabilities that make the rounding unbiased, so that updates
- * smaller than half an FP16 step accumulate in expectation; 0 rounds to nearest), "adjoint_fp64" (0 or 1: arithmetic of lbm_adjoint_step's vector-Jacobian products),
+ * smaller than half an FP16 step accumulate in expectation; 0 rounds to nearest), "adjoint_arith" (arithmetic of lbm_adjoint_step's vector-Jacobian products and adjoint state: 2, the default, double-float, i.e. pairs of FP32
+ * numbers with a 48-bit significand evaluated on the FP32 pipes; 1 FP64; 0 FP32), "adjoint_fp64" (0 or 1: the same as "adjoint_arith" 0 or 1),
  * "graph_steps" (even count of steps that lbm_step replays as one CUDA graph; 0 disables), or the
  * thread-block shape of the step launch, "block_x" (32, 64, 128 or 256) and "block_y"
  * (block_x * block_y <= 256), or "tma_rows" (0 = off; 1, 2 or 4: the 3D FP32 / FP16S step stages
@@ -197,8 +198,10 @@ LBM_API int lbm_set_wall_profile(lbm_handle h, int face, const double* T_w, long
  * K = ceil(sqrt(n_steps)) steps, then n_steps fused adjoint steps backward, recomputing each
  * segment of K states once from its checkpoint: about 2 sqrt(n_steps) states of device memory and
  * one extra forward pass.  The vector-Jacobian products of the collision are evaluated at the
- * stored states in FP64 (lbm_set_param "adjoint_fp64" = 0 selects FP32 arithmetic: about 6 times
- * faster, gradients to about 1e-4 relative after 2000 steps); the design gradient is always
+ * stored states in double-float arithmetic by default: the gradient equals the FP64 adjoint's to
+ * about 1e-12 relative, at a third of its cost on GPUs whose FP64 rate is a small fraction of
+ * their FP32 rate.  lbm_set_param "adjoint_arith" = 1 selects FP64, 0 FP32 (about twice as fast
+ * again, gradients to about 1e-4 relative after 2000 steps).  The design gradient is always
  * accumulated in FP64.  2D (D2Q9 pair) only.
  * J and grad_Tw are host pointers; n must equal the number of design-face nodes.
  * Errors: LBM_EINVAL (bad faces, n, n_steps), LBM_ENOTSUP (3D), LBM_ENOMEM, LBM_ECUDA.

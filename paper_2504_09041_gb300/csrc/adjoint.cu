@@ -4,13 +4,17 @@
 
 namespace lbm {
 
-cudaError_t launch_adjoint_seed(const Geometry& geo, int face, double scale, void* mu, bool fp64,
+cudaError_t launch_adjoint_seed(const Geometry& geo, int face, double scale, void* mu, int arith,
                                 cudaStream_t st)
 {
     const int n_face = (face >> 1) == 0 ? geo.ny : geo.nx;
     const int nb = (n_face + 127) / 128;
-    if (fp64) adjoint_seed_d2q9_kernel<double><<<nb, 128, 0, st>>>((double*)mu, geo, face, scale);
-    else adjoint_seed_d2q9_kernel<float><<<nb, 128, 0, st>>>((float*)mu, geo, face, scale);
+    switch (arith) {
+    case kAdjF64: adjoint_seed_d2q9_kernel<double><<<nb, 128, 0, st>>>((double*)mu, geo, face, scale); break;
+    case kAdjF32: adjoint_seed_d2q9_kernel<float><<<nb, 128, 0, st>>>((float*)mu, geo, face, scale); break;
+    case kAdjDF: adjoint_seed_d2q9_kernel<dfloat><<<nb, 128, 0, st>>>((dfloat*)mu, geo, face, scale); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -29,14 +33,18 @@ static cudaError_t run_adjoint(const void* f_prev, const void* g_prev, const voi
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_step_d2q9(int prec, bool fp64, const void* f_prev, const void* g_prev,
+cudaError_t launch_adjoint_step_d2q9(int prec, int arith, const void* f_prev, const void* g_prev,
                                      const void* mu_in, void* mu_out, const Geometry& geo,
                                      const HostCoeffs& hc, int design_face, double* grad,
                                      cudaStream_t st)
 {
 #define LBM_ADJ(S)                                                                                  \
-    return fp64 ? run_adjoint<S, double>(f_prev, g_prev, mu_in, mu_out, geo, hc, design_face, grad, st) \
-                : run_adjoint<S, float>(f_prev, g_prev, mu_in, mu_out, geo, hc, design_face, grad, st)
+    switch (arith) {                                                                                \
+    case kAdjF64: return run_adjoint<S, double>(f_prev, g_prev, mu_in, mu_out, geo, hc, design_face, grad, st); \
+    case kAdjF32: return run_adjoint<S, float>(f_prev, g_prev, mu_in, mu_out, geo, hc, design_face, grad, st);  \
+    case kAdjDF: return run_adjoint<S, dfloat>(f_prev, g_prev, mu_in, mu_out, geo, hc, design_face, grad, st); \
+    }                                                                                               \
+    return cudaErrorInvalidValue
     switch (prec) {
     case kF64: LBM_ADJ(StoreF64);
     case kF32: LBM_ADJ(StoreF32);

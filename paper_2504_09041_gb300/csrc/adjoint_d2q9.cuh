@@ -11,8 +11,12 @@
 // neighbours' mu, recomputes the forward pull and collision of its node from the stored state in
 // the adjoint arithmetic type RT, and applies the hand-written vector-Jacobian product of the
 // collision.  The design gradient is always accumulated in FP64.
+//
+// RT is double, float or dfloat (double-float, dfloat.cuh): the VJP is written once with the
+// arithmetic operators and instantiated for each.
 #pragma once
 
+#include "dfloat.cuh"
 #include "step_d2q9.cuh"
 
 namespace lbm {

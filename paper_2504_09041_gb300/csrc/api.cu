@@ -51,7 +51,7 @@ struct lbm_s {
     unsigned* status = nullptr;
     cudaStream_t stream = nullptr;
     int block_x = 0, block_y = 0;   // launch shape of the step kernel (0: default)
-    int adjoint_fp64 = 1;           // arithmetic of the adjoint's vector-Jacobian products
+    int adjoint_arith = 2;          // arithmetic of the adjoint's VJPs: 0 FP32, 1 FP64, 2 double-float
     int tma_rows = 0;               // 3D FP32/FP16S: TMA-staged step with tiles of 64 x tma_rows
     lbm::TmaMaps tm[2];             // tensor maps of the input buffers f[c], g[c]
     // CUDA graphs of graph_steps consecutive steps (even, so the A/B parity returns), one per
@@ -450,7 +450,13 @@ int lbm_set_param(lbm_handle h, const char* key, double v)
     }
     if (k == "adjoint_fp64") {
         if (!(v == 0.0 || v == 1.0)) return fail(h, LBM_EINVAL, "adjoint_fp64 must be 0 or 1");
-        h->adjoint_fp64 = (int)v;
+        h->adjoint_arith = (int)v;
+        return LBM_OK;
+    }
+    if (k == "adjoint_arith") {
+        if (!(v == 0.0 || v == 1.0 || v == 2.0))
+            return fail(h, LBM_EINVAL, "adjoint_arith must be 0 (FP32), 1 (FP64) or 2 (double-float)");
+        h->adjoint_arith = (int)v;
         return LBM_OK;
     }
     if (k == "gbeta" || k == "T_ref") {
@@ -696,7 +702,7 @@ int lbm_adjoint_step(lbm_handle h, long n_steps, int objective_face, int design_
     std::vector<void*> ckf(nck, nullptr), ckg(nck, nullptr), sgf(K, nullptr), sgg(K, nullptr);
     void* mu[2] = {nullptr, nullptr};
     double* grad = nullptr;
-    const bool afp64 = h->adjoint_fp64 != 0;
+    const int arith = h->adjoint_arith;
     auto cleanup = [&]() {
         cudaStreamSynchronize(h->stream);
         for (auto p : ckf) dev_free(h, p);
@@ -710,7 +716,7 @@ int lbm_adjoint_step(lbm_handle h, long n_steps, int objective_face, int design_
     bool ok = true;
     for (long m = 0; m < nck && ok; ++m) ok = (ckf[m] = dev_alloc(h, fb)) && (ckg[m] = dev_alloc(h, gb));
     for (long r = 1; r < K && ok; ++r) ok = (sgf[r] = dev_alloc(h, fb)) && (sgg[r] = dev_alloc(h, gb));
-    const size_t mub = (size_t)(h->qf + h->qg) * h->geo.n * (afp64 ? sizeof(double) : sizeof(float));
+    const size_t mub = (size_t)(h->qf + h->qg) * h->geo.n * (arith == lbm::kAdjF32 ? sizeof(float) : 8);
     ok = ok && (mu[0] = dev_alloc(h, mub)) && (mu[1] = dev_alloc(h, mub)) &&
          (grad = (double*)dev_alloc(h, sizeof(double) * n));
     if (!ok) {
@@ -751,7 +757,7 @@ int lbm_adjoint_step(lbm_handle h, long n_steps, int objective_face, int design_
     int a = 0;
     ADJ_CK(cudaMemsetAsync(mu[a], 0, mub, h->stream));
     ADJ_CK(cudaMemsetAsync(grad, 0, sizeof(double) * n, h->stream));
-    ADJ_CK(lbm::launch_adjoint_seed(h->geo, objective_face, scale, mu[a], afp64, h->stream));
+    ADJ_CK(lbm::launch_adjoint_seed(h->geo, objective_face, scale, mu[a], arith, h->stream));
     // backward over the segments, last first
     for (long m = nck - 1; m >= 0; --m) {
         const long lo = m * K, hi = std::min((m + 1) * K, n_steps);
@@ -765,7 +771,7 @@ int lbm_adjoint_step(lbm_handle h, long n_steps, int objective_face, int design_
             sg[r2] = sgg[r2];
         }
         for (long k = hi; k >= lo + 1; --k) {
-            ADJ_CK(lbm::launch_adjoint_step_d2q9(h->prec, afp64, sf[k - 1 - lo], sg[k - 1 - lo], mu[a],
+            ADJ_CK(lbm::launch_adjoint_step_d2q9(h->prec, arith, sf[k - 1 - lo], sg[k - 1 - lo], mu[a],
                                                  mu[1 - a], h->geo, h->hc, design_face, grad,
                                                  h->stream));
             a = 1 - a;

@@ -94,11 +94,12 @@ cudaError_t launch_nusselt(int dim, int prec, const void* f, const void* g, cons
 
 // Adjoint of the D2Q9 step (adjoint_d2q9.cuh): seed mu_{n+1} = dJ/dp for J = mean Nu on `face`
 // (mu must be zeroed first), and one fused adjoint step mu_{k+1} -> mu_k from the state s_{k-1},
-// adding the design-face wall-temperature gradient (FP64) to grad.  mu holds FP64 values when
-// fp64 is set, FP32 otherwise.
-cudaError_t launch_adjoint_seed(const Geometry& geo, int face, double scale, void* mu, bool fp64,
+// adding the design-face wall-temperature gradient (FP64) to grad.  `arith` is the arithmetic of
+// the vector-Jacobian products and of mu: FP32 (4-byte mu), FP64 or double-float (8-byte mu).
+enum AdjointArith { kAdjF32 = 0, kAdjF64 = 1, kAdjDF = 2 };
+cudaError_t launch_adjoint_seed(const Geometry& geo, int face, double scale, void* mu, int arith,
                                 cudaStream_t st);
-cudaError_t launch_adjoint_step_d2q9(int prec, bool fp64, const void* f_prev, const void* g_prev,
+cudaError_t launch_adjoint_step_d2q9(int prec, int arith, const void* f_prev, const void* g_prev,
                                      const void* mu_in, void* mu_out, const Geometry& geo,
                                      const HostCoeffs& hc, int design_face, double* grad,
                                      cudaStream_t st);

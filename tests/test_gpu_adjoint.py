@@ -14,7 +14,10 @@
     linearises about the FP32 trajectory, whose rounding moves the smallest gradient components
     by a few 1e-4 of themselves; there the error of each directional derivative is bounded by
     1e-4 of its Cauchy-Schwarz scale |grad| |v| (the relative error of the gradient vector).
-  * The FP32 adjoint arithmetic (adjoint_fp64 = 0) against the FP64 default on that workload.
+  * The FP32 adjoint arithmetic (adjoint_fp64 = 0) against the FP64 adjoint on that workload.
+  * Double-float arithmetic (adjoint_arith = 2, pairs of FP32 numbers with a 48-bit significand)
+    is held to every FP64 bar above, and to the FP64 adjoint's gradient within 1e-10 of its
+    largest component on the 2000-step workload.
   * The torch.autograd.Function wrapper returns the same gradient.
   * The oracle adjoint: directional derivatives of the generic-form oracle by complex step, exact
     to rounding, against the GPU gradient (FP64 states) within 1e-8 relative, options A and B.
@@ -35,6 +38,8 @@ if not torch.cuda.is_available():
 from paper_2504_09041_gb300 import lbm as L  # noqa: E402
 
 HOT, COLD = 0, 1
+# adjoint arithmetic held to the FP64 bars: 1 = FP64, 2 = double-float (FP32 pairs)
+ARITH = [1, 2]
 
 
 def oracle_J(nx, ny, Ra, prof, steps):
@@ -44,10 +49,12 @@ def oracle_J(nx, ny, Ra, prof, steps):
     return o.nusselt(COLD)[0]
 
 
-def test_adjoint_matches_oracle_finite_differences():
+@pytest.mark.parametrize("arith", ARITH)
+def test_adjoint_matches_oracle_finite_differences(arith):
     nx, ny, steps, Ra, h = 24, 20, 150, 1e5, 1e-2
     prof = synth.sine_profile(5, ny)
     lat = L.Lattice("d2q9", nx, ny, Ra=Ra, walls=L.Walls.cavity(2), precision="fp64")
+    lat.set_param("adjoint_arith", arith)
     lat.set_wall_profile(HOT, prof)
     J, grad = lat.adjoint(steps, COLD, HOT)
     assert J == pytest.approx(oracle_J(nx, ny, Ra, prof, steps), abs=1e-11)
@@ -60,7 +67,8 @@ def test_adjoint_matches_oracle_finite_differences():
     np.testing.assert_allclose(grad, fd, rtol=0, atol=1e-6 * scale)
 
 
-def test_adjoint_option_b_matches_oracle_finite_differences():
+@pytest.mark.parametrize("arith", ARITH)
+def test_adjoint_option_b_matches_oracle_finite_differences(arith):
     """The option-B energy attractors (Eq. MvT2DoptionB) with second-order energy rates away from
     1, so that they differ from option A: adjoint against oracle central differences."""
     nx, ny, steps, Ra, h = 22, 18, 120, 1e5, 1e-2
@@ -78,6 +86,7 @@ def test_adjoint_option_b_matches_oracle_finite_differences():
     lat = L.Lattice("d2q9", nx, ny, Ra=Ra, walls=L.Walls.cavity(2), precision="fp64")
     lat.set_omegas(None, om_g)
     lat.set_param("g_attractors", 1)
+    lat.set_param("adjoint_arith", arith)
     lat.set_wall_profile(HOT, prof)
     J, grad = lat.adjoint(steps, COLD, HOT)
     assert J == pytest.approx(J_of(prof), abs=1e-11)
@@ -90,8 +99,9 @@ def test_adjoint_option_b_matches_oracle_finite_differences():
     np.testing.assert_allclose(grad, fd, rtol=0, atol=1e-6 * scale)
 
 
+@pytest.mark.parametrize("arith", ARITH)
 @pytest.mark.parametrize("g_option", [0, 1])
-def test_adjoint_matches_the_complex_step_oracle(g_option):
+def test_adjoint_matches_the_complex_step_oracle(g_option, arith):
     """grad . v from lbm_adjoint_step against Im(J(T_w + i h v)) / h of the generic-form oracle."""
     nx, ny, steps, Ra = 24, 20, 150, 1e5
     bc = O.cavity_bc(2)
@@ -105,6 +115,7 @@ def test_adjoint_matches_the_complex_step_oracle(g_option):
     lat = L.Lattice("d2q9", nx, ny, Ra=Ra, walls=L.Walls.cavity(2), precision="fp64")
     lat.set_omegas(None, om_g)
     lat.set_param("g_attractors", g_option)
+    lat.set_param("adjoint_arith", arith)
     lat.set_wall_profile(HOT, prof)
     J, grad = lat.adjoint(steps, COLD, HOT)
 
@@ -123,8 +134,8 @@ def test_adjoint_matches_the_complex_step_oracle(g_option):
 
 
 def test_adjoint_handles_uneven_segments_and_fp32():
-    """47 steps (segments of 7, the last one shorter), FP32 states and FP64 adjoint, against the
-    FP64 adjoint on the same problem."""
+    """47 steps (segments of 7, the last one shorter), FP32 states against FP64 states on the same
+    problem (default adjoint arithmetic)."""
     nx, ny = 30, 26
     prof = synth.sine_profile(8, ny)
     grads = {}
@@ -160,14 +171,16 @@ def workload_fd():
     return prof, [v for v, _ in dirs], fds
 
 
+@pytest.mark.parametrize("arith", ARITH)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_adjoint_256_2000_steps_matches_central_differences(precision, workload_fd):
+def test_adjoint_256_2000_steps_matches_central_differences(precision, arith, workload_fd):
     """The adjoint workload: 256^2 cavity, Ra 1e5, 2000 steps, hot-wall profile 1 + 0.05 * seeded
     sine modes, J = mean cold-wall Nu; FP64 adjoint accumulation; FD of the FP64 forward."""
     nx = ny = 256
     steps, Ra = 2000, 1e5
     prof, dirs, fds = workload_fd
     lat = L.Lattice("d2q9", nx, ny, Ra=Ra, walls=L.Walls.cavity(2), precision=precision)
+    lat.set_param("adjoint_arith", arith)
     lat.set_wall_profile(HOT, prof)
     J, grad = lat.adjoint(steps, COLD, HOT)
     gn = np.linalg.norm(grad)
@@ -212,3 +225,31 @@ def test_fp32_adjoint_arithmetic_stated_accuracy():
         grads[flag] = lat.adjoint(2000, COLD, HOT)[1]
         lat.close()
     np.testing.assert_allclose(grads[0], grads[1], rtol=0, atol=1e-4 * np.abs(grads[1]).max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_double_float_adjoint_equals_fp64_adjoint(precision):
+    """adjoint_arith = 2 against the FP64 adjoint on the 256^2, 2000-step workload: the gradients
+    agree within 1e-10 of the largest component (each VJP operation carries a relative error of a
+    few 2^-48, and the adjoint is linear in mu, so the difference stays at that level)."""
+    nx = ny = 256
+    prof = synth.sine_profile(2024, ny)
+    grads = {}
+    for arith in (1, 2):
+        lat = L.Lattice("d2q9", nx, ny, Ra=1e5, walls=L.Walls.cavity(2), precision=precision)
+        lat.set_wall_profile(HOT, prof)
+        lat.set_param("adjoint_arith", arith)
+        grads[arith] = lat.adjoint(2000, COLD, HOT)[1]
+        lat.close()
+    scale = np.abs(grads[1]).max()
+    err = np.abs(grads[2] - grads[1]).max()
+    assert err <= 1e-10 * scale, err / scale
+
+
+def test_adjoint_arith_rejects_unknown_values():
+    lat = L.Lattice("d2q9", 16, 12, Ra=1e4, walls=L.Walls.cavity(2), precision="fp32")
+    for bad in (3, 1.5, -1):
+        with pytest.raises(L.LbmError):
+            lat.set_param("adjoint_arith", bad)
+    lat.set_param("adjoint_arith", 2)
+    lat.close()
