@@ -243,9 +243,10 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t_e2e = reduce_max(time.perf_counter() - t0, world)
 
-    forms, adjoint, batched = [], None, None
+    forms, adjoint, batched, nu_acc = [], None, None, None
     if world == 1 and not args.no_forms:
         forms = measure_forms(L, torch, stream, args)
+        nu_acc = measure_nu_accuracy(L, stream)
         batched = measure_batched(L, torch, stream)
         adjoint = measure_adjoint(L, torch, stream)
 
@@ -310,6 +311,8 @@ def run_gpu(args):
     }
     if forms:
         line["per_form"] = forms
+    if nu_acc:
+        line["nu_accuracy"] = nu_acc
     if batched:
         line["batched"] = batched
     if adjoint:
@@ -367,6 +370,27 @@ def measure_forms(L, torch, stream, args):
             rec["roofline"] = fp64_alu_roofline(lat.n / s / 1e6, lat_name)
         out.append(rec)
         lat.close()
+    return out
+
+
+def measure_nu_accuracy(L, stream):
+    """Mean hot-wall Nu of the FP32 and FP16-storage forms against the FP64 form on the same GPU:
+    the 64^2 cavity at Ra 1e4 after 20,000 steps (steady) and a 32^3 cavity at Ra 1e5 after
+    20,000 steps."""
+    cases = [("2D cavity 64x64, Ra 1e4, Pr 0.71, 20000 steps", "d2q9", 64, 64, 1, 1e4, 2),
+             ("3D cavity 32^3, Ra 1e5, Pr 0.71, 20000 steps", "d3q27", 32, 32, 32, 1e5, 3)]
+    out = []
+    for label, lat_name, nx, ny, nz, Ra, dim in cases:
+        nu = {}
+        for prec in ("fp64", "fp32", "fp16s"):
+            lat = L.Lattice(lat_name, nx, ny, nz, Ra, 0.71, 0.1, walls=L.Walls.cavity(dim),
+                            precision=prec, stream=stream)
+            lat.step(20000)
+            lat.sync()
+            nu[prec] = lat.nusselt(0)[0]
+            lat.close()
+        out.append({"case": label, "nu_hot_mean": nu,
+                    "rel_vs_fp64": {p: abs(nu[p] - nu["fp64"]) / abs(nu["fp64"]) for p in ("fp32", "fp16s")}})
     return out
 
 

@@ -735,15 +735,17 @@ int lbm_adjoint_step(lbm_handle h, long n_steps, int objective_face, int design_
     // forward pass with checkpoints s_0, s_K, s_2K, ...
     ADJ_CK(cudaMemcpyAsync(ckf[0], h->f[h->cur], fb, cudaMemcpyDeviceToDevice, h->stream));
     ADJ_CK(cudaMemcpyAsync(ckg[0], h->g[h->cur], gb, cudaMemcpyDeviceToDevice, h->stream));
-    for (long k = 1; k <= n_steps; ++k) {
-        const int c = h->cur;
-        ADJ_CK(lbm::launch_step(h->dim, h->prec, h->f[c], h->g[c], h->f[1 - c], h->g[1 - c], h->geo,
-                                h->hc, h->status, blk, h->stream));
-        h->cur = 1 - c;
-        ++h->steps;
-        if (k % K == 0 && k / K < nck) {
-            ADJ_CK(cudaMemcpyAsync(ckf[k / K], h->f[h->cur], fb, cudaMemcpyDeviceToDevice, h->stream));
-            ADJ_CK(cudaMemcpyAsync(ckg[k / K], h->g[h->cur], gb, cudaMemcpyDeviceToDevice, h->stream));
+    // (each segment through lbm_step, which replays its CUDA graphs)
+    for (long m = 1; m <= nck; ++m) {
+        const long len = std::min(m * K, n_steps) - (m - 1) * K;
+        const int rc = lbm_step(h, len);
+        if (rc) {
+            cleanup();
+            return rc;
+        }
+        if (m < nck) {
+            ADJ_CK(cudaMemcpyAsync(ckf[m], h->f[h->cur], fb, cudaMemcpyDeviceToDevice, h->stream));
+            ADJ_CK(cudaMemcpyAsync(ckg[m], h->g[h->cur], gb, cudaMemcpyDeviceToDevice, h->stream));
         }
     }
     // objective at the final state
