@@ -406,7 +406,7 @@ def measure_batched(L, torch, stream, steps: int = 2000, unbatched_steps: int = 
     peak, _ = hbm_peak()
     b = L.Batch(sizes, Ra, Pr, Ma=0.1, precision="fp32", stream=stream)
     t0 = time.perf_counter()
-    tx, ty, cps = b.tune(10)
+    tx, ty, cps = b.tune(20)
     tune_s = time.perf_counter() - t0
     b.step(64)
     b.sync()

@@ -312,14 +312,14 @@ LBM_API int lbm_batch_destroy(lbm_batch b);
 LBM_API int lbm_batch_set_stream(lbm_batch b, void* stream);
 
 /* Launch shape of the step: tiles of tile_x x tile_y nodes (tile_x in {32, 64, 128, 256},
- * tile_x * tile_y <= 256 threads), ctas_per_sm blocks per SM (1..64; 0 = as many as the SM holds
+ * tile_x * tile_y <= 256 threads), ctas_per_sm blocks per SM (1..1024; 0 = as many as the SM holds
  * at once, so that every block is resident and takes one equal share of the tiles), and
  * graph_steps steps per CUDA graph replay (0..4096, rounded up to even; 0 = plain launches).
  * Default 64 x 2 tiles, ctas_per_sm 0, 32 graph steps.  Errors: LBM_EINVAL for another shape. */
 LBM_API int lbm_batch_set_launch(lbm_batch b, int tile_x, int tile_y, int ctas_per_sm, int graph_steps);
 
-/* Autotuner: time trial_steps steps of every tile shape of a fixed list, each with half, all and
- * twice the blocks per SM that the SM holds at once (CUDA occupancy API), on a device copy of the
+/* Autotuner: time trial_steps steps of every tile shape of a fixed list, each with 1/2 to 64
+ * times (at most 1024) the blocks per SM that the SM holds at once (CUDA occupancy API), on a device copy of the
  * current populations; keep the fastest and report it through the optional outputs.  The batch's own state and step count are unchanged (divergence flags are
  * cleared).  Needs device memory for two extra copies of the populations (LBM_ENOMEM otherwise). */
 LBM_API int lbm_batch_tune(lbm_batch b, int trial_steps, int* tile_x, int* tile_y, int* ctas_per_sm);

@@ -256,7 +256,7 @@ int valid_launch(int tx, int ty, int cps)
 {
     const int threads = tx * ty;
     return (tx == 32 || tx == 64 || tx == 128 || tx == 256) && ty >= 1 && threads <= 256 &&
-           cps >= 0 && cps <= 64;
+           cps >= 0 && cps <= 1024;
 }
 
 size_t elem_bytes(int prec) { return lbm::storage_bytes(prec); }
@@ -438,7 +438,8 @@ int lbm_batch_tune(lbm_batch b, int trial_steps, int* tile_x, int* tile_y, int* 
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    // each tile shape with half, all and twice the blocks that are resident on an SM at once
+    // each tile shape with 1/2 to 64 times the blocks that are resident on an SM at once (at most
+    // 1024): oversubscribed grids let the block scheduler even out the uneven members
     const int shapes[][2] = {{32, 2}, {32, 4}, {64, 1}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}};
     const int keep[3] = {b->tile_x, b->tile_y, b->ctas_per_sm};
     float best = INFINITY;
@@ -448,9 +449,12 @@ int lbm_batch_tune(lbm_batch b, int trial_steps, int* tile_x, int* tile_y, int* 
     cudaMemcpyAsync(tg[0], b->g[b->cur], bytes, cudaMemcpyDeviceToDevice, b->stream);
     for (auto& sh : shapes) {
         const int occ = max_resident(b->prec, sh[0] * sh[1]);
-        const int ctas[3] = {std::max(1, occ / 2), occ, 2 * occ};
+        const int ctas[8] = {std::max(1, occ / 2), occ, 2 * occ, 4 * occ, 8 * occ, 16 * occ, 32 * occ, 64 * occ};
+        int last = 0;
         for (int cps : ctas) {
-            if (!valid_launch(sh[0], sh[1], cps)) continue;
+            cps = std::min(cps, 1024);
+            if (cps == last || !valid_launch(sh[0], sh[1], cps)) continue;
+            last = cps;
             b->tile_x = sh[0];
             b->tile_y = sh[1];
             b->ctas_per_sm = cps;
