@@ -395,7 +395,7 @@ def measure_nu_accuracy(L, stream):
 
 
 def measure_batched(L, torch, stream, steps: int = 2000, unbatched_steps: int = 256,
-                    compare: bool = True):
+                    compare: bool = True, launch=None):
     """The ensemble workload: 64 independent square cavities (sides 64..512, Ra log-uniform in
     [1e3, 1e7], Pr uniform in [0.71, 7], seeded), FP32, one autotuned persistent launch per
     step replayed from CUDA graphs.  Compared with the same members advanced one handle at a
@@ -406,7 +406,11 @@ def measure_batched(L, torch, stream, steps: int = 2000, unbatched_steps: int = 
     peak, _ = hbm_peak()
     b = L.Batch(sizes, Ra, Pr, Ma=0.1, precision="fp32", stream=stream)
     t0 = time.perf_counter()
-    tx, ty, cps = b.tune(20)
+    if launch:
+        tx, ty, cps = launch
+        b.set_launch(tx, ty, cps)
+    else:
+        tx, ty, cps = b.tune(20)
     tune_s = time.perf_counter() - t0
     b.step(64)
     b.sync()
@@ -480,7 +484,8 @@ def run_only(args):
     from paper_2504_09041_gb300 import lbm as L
     stream = torch.cuda.Stream()
     if args.only == "batched":
-        return measure_batched(L, torch, stream, steps=args.steps, compare=False)
+        launch = tuple(int(v) for v in args.batch_launch.split("x")) if args.batch_launch else None
+        return measure_batched(L, torch, stream, steps=args.steps, compare=False, launch=launch)
     return measure_adjoint(L, torch, stream)
 
 
@@ -658,7 +663,11 @@ def main(argv=None):
     ap.add_argument("--nz", type=int, default=None)
     ap.add_argument("--only", default=None, choices=["batched", "adjoint"],
                     help="run one secondary measurement alone and print its record (profiling)")
+    ap.add_argument("--batch-launch", default=None,
+                    help="with --only batched: fixed launch TXxTYxCPS instead of the autotuner (profiling)")
     args = ap.parse_args(argv)
+    if args.batch_launch and (args.only != "batched" or len(args.batch_launch.split("x")) != 3):
+        ap.error("--batch-launch takes TXxTYxCPS and needs --only batched")
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.lattice == "d2q9":
