@@ -698,13 +698,15 @@ int lbm_adjoint_step(lbm_handle h, long n_steps, int objective_face, int design_
     const size_t fb = (size_t)h->qf * h->geo.n * sb, gb = (size_t)h->qg * h->geo.n * sb;
     const long K = (long)std::ceil(std::sqrt((double)n_steps));
     const long nck = (n_steps + K - 1) / K;
-    // device memory: nck checkpoints, K - 1 segment states, two adjoint buffers, the gradient
+    // device memory: nck checkpoints, K segment states, two adjoint buffers, the gradient
     std::vector<void*> ckf(nck, nullptr), ckg(nck, nullptr), sgf(K, nullptr), sgg(K, nullptr);
     void* mu[2] = {nullptr, nullptr};
     double* grad = nullptr;
     const int arith = h->adjoint_arith;
+    cudaGraphExec_t seg_exec = nullptr;
     auto cleanup = [&]() {
         cudaStreamSynchronize(h->stream);
+        if (seg_exec) cudaGraphExecDestroy(seg_exec);
         for (auto p : ckf) dev_free(h, p);
         for (auto p : ckg) dev_free(h, p);
         for (auto p : sgf) dev_free(h, p);
@@ -715,7 +717,9 @@ int lbm_adjoint_step(lbm_handle h, long n_steps, int objective_face, int design_
     };
     bool ok = true;
     for (long m = 0; m < nck && ok; ++m) ok = (ckf[m] = dev_alloc(h, fb)) && (ckg[m] = dev_alloc(h, gb));
-    for (long r = 1; r < K && ok; ++r) ok = (sgf[r] = dev_alloc(h, fb)) && (sgg[r] = dev_alloc(h, gb));
+    // segment states 1 .. K-1, and state 0: the copy of a checkpoint that the recompute graph reads
+    const bool seg_graph = K >= 3;
+    for (long r = seg_graph ? 0 : 1; r < K && ok; ++r) ok = (sgf[r] = dev_alloc(h, fb)) && (sgg[r] = dev_alloc(h, gb));
     const size_t mub = (size_t)(h->qf + h->qg) * h->geo.n * (arith == lbm::kAdjF32 ? sizeof(float) : 8);
     ok = ok && (mu[0] = dev_alloc(h, mub)) && (mu[1] = dev_alloc(h, mub)) &&
          (grad = (double*)dev_alloc(h, sizeof(double) * n));
@@ -760,17 +764,43 @@ int lbm_adjoint_step(lbm_handle h, long n_steps, int objective_face, int design_
     ADJ_CK(cudaMemsetAsync(mu[a], 0, mub, h->stream));
     ADJ_CK(cudaMemsetAsync(grad, 0, sizeof(double) * n, h->stream));
     ADJ_CK(lbm::launch_adjoint_seed(h->geo, objective_face, scale, mu[a], arith, h->stream));
+    // The K - 1 recompute steps of a full segment, state 0 -> 1 -> ... -> K - 1 of the segment
+    // buffers, captured once as a CUDA graph; each full segment copies its checkpoint into state 0
+    // and replays it.
+    if (seg_graph) {
+        if (!h->capture_stream) ADJ_CK(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        ADJ_CK(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (long r2 = 1; r2 < K && e == cudaSuccess; ++r2)
+            e = lbm::launch_step(h->dim, h->prec, sgf[r2 - 1], sgg[r2 - 1], sgf[r2], sgg[r2], h->geo, h->hc,
+                                 h->status, blk, h->capture_stream);
+        const cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
+        if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&seg_exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        ADJ_CK(e != cudaSuccess ? e : e2);
+    }
     // backward over the segments, last first
     for (long m = nck - 1; m >= 0; --m) {
         const long lo = m * K, hi = std::min((m + 1) * K, n_steps);
         std::vector<const void*> sf(hi - lo), sg(hi - lo);
         sf[0] = ckf[m];
         sg[0] = ckg[m];
-        for (long r2 = 1; r2 < hi - lo; ++r2) {
-            ADJ_CK(lbm::launch_step(h->dim, h->prec, sf[r2 - 1], sg[r2 - 1], sgf[r2], sgg[r2], h->geo,
-                                    h->hc, h->status, blk, h->stream));
-            sf[r2] = sgf[r2];
-            sg[r2] = sgg[r2];
+        if (seg_graph && hi - lo == K) {
+            ADJ_CK(cudaMemcpyAsync(sgf[0], ckf[m], fb, cudaMemcpyDeviceToDevice, h->stream));
+            ADJ_CK(cudaMemcpyAsync(sgg[0], ckg[m], gb, cudaMemcpyDeviceToDevice, h->stream));
+            ADJ_CK(cudaGraphLaunch(seg_exec, h->stream));
+            for (long r2 = 1; r2 < K; ++r2) {
+                sf[r2] = sgf[r2];
+                sg[r2] = sgg[r2];
+            }
+        } else {
+            for (long r2 = 1; r2 < hi - lo; ++r2) {
+                ADJ_CK(lbm::launch_step(h->dim, h->prec, sf[r2 - 1], sg[r2 - 1], sgf[r2], sgg[r2], h->geo,
+                                        h->hc, h->status, blk, h->stream));
+                sf[r2] = sgf[r2];
+                sg[r2] = sgg[r2];
+            }
         }
         for (long k = hi; k >= lo + 1; --k) {
             ADJ_CK(lbm::launch_adjoint_step_d2q9(h->prec, arith, sf[k - 1 - lo], sg[k - 1 - lo], mu[a],
