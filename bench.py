@@ -325,7 +325,7 @@ def run_gpu(args):
 
 # FP64 lane operations per node update of the FP64 steps (ncu counts in
 # profiles/flops_step_d3q27.md) and GB300's FP64 pipe rate: 2 lane operations per SM per clock.
-FP64_OPS_PER_NODE = {"d3q27": 1008.9, "d2q9": 340.6}
+FP64_OPS_PER_NODE = {"d3q27": 973.8, "d2q9": 340.6}
 FP64_LANE_OPS_PER_SM_CLK = 2
 
 
