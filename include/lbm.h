@@ -138,7 +138,9 @@ LBM_API int lbm_set_omegas(lbm_handle h, const double* om_f, int n_f, const doub
  * stochastically, up or down with probabilities that make the rounding unbiased, so that updates
  * smaller than half an FP16 step accumulate in expectation; 0 rounds to nearest), "adjoint_arith" (arithmetic of lbm_adjoint_step's vector-Jacobian products and adjoint state: 2, the default, double-float, i.e. pairs of FP32
  * numbers with a 48-bit significand evaluated on the FP32 pipes; 1 FP64; 0 FP32), "adjoint_fp64" (0 or 1: the same as "adjoint_arith" 0 or 1),
- * "graph_steps" (even count of steps that lbm_step replays as one CUDA graph; 0 disables), or the
+ * "graph_steps" (even count of steps that lbm_step replays as one CUDA graph; 0 disables),
+ * "index64" (1: the step kernels use 64-bit element offsets, the instantiation that boxes with
+ * q n >= 2^32 run, on any box; results are bitwise those of the 32-bit form; for testing that path), or the
  * thread-block shape of the step launch, "block_x" (32, 64, 128 or 256) and "block_y"
  * (block_x * block_y <= 256), or "tma_rows" (0 = off; 1, 2 or 4: the 3D FP32 / FP16S step stages
  * its pull through shared memory with tensor copies in tiles of 64 x tma_rows nodes; results are

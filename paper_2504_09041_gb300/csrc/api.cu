@@ -438,6 +438,11 @@ int lbm_set_param(lbm_handle h, const char* key, double v)
         h->tma_rows = v_i;
         return LBM_OK;
     }
+    if (k == "index64") {
+        if (!(v == 0.0 || v == 1.0)) return fail(h, LBM_EINVAL, "index64 must be 0 or 1");
+        h->hc.index64 = (int)v;
+        return LBM_OK;
+    }
     if (k == "fp16_stochastic") {
         if (!(v == 0.0 || v == 1.0)) return fail(h, LBM_EINVAL, "fp16_stochastic must be 0 or 1");
         h->hc.fp16_sr = (int)v;

@@ -21,6 +21,7 @@ struct HostCoeffs {
     int gaxis;
     int gopt;   // energy attractors of orders 3-4: 0 = option A, 1 = option B
     int fp16_sr;   // F16S storage: stochastic (1) or nearest (0) rounding of stored deviations
+    int index64;   // 1: the step uses 64-bit element offsets even where 32-bit ones suffice
 };
 
 size_t storage_bytes(int prec);
@@ -141,6 +142,13 @@ inline dim3 block_shape(int nx, dim3 chosen = dim3(0, 0, 0), int dim = 2)
 inline bool index32(const Geometry& g, int q)
 {
     return (unsigned long long)q * (unsigned long long)g.n <= 0xffffffffULL;
+}
+
+// The step's offset width: 32-bit where q n < 2^32, unless the handle forces the 64-bit
+// instantiation (which boxes above that size run; forcing it lets small boxes test it).
+inline bool step_index32(const Geometry& g, int q, const HostCoeffs& hc)
+{
+    return index32(g, q) && !hc.index64;
 }
 
 inline dim3 grid_shape(const Geometry& g, dim3 b)

@@ -13,7 +13,7 @@ static cudaError_t run(const void* fin, const void* gin, void* fout, void* gout,
     const dim3 b = block_shape(geo.nx, block);
     const dim3 grid((geo.nx + b.x - 1) / b.x, (geo.ny + b.y - 1) / b.y, 1);
     const auto c = make_coeffs<R, 9, 9>(hc);
-    if (index32(geo, 9))
+    if (step_index32(geo, 9, hc))
         step_d2q9_kernel<S, unsigned><<<grid, b, 0, st>>>((const T*)fin, (const T*)gin, (T*)fout,
                                                           (T*)gout, geo, c, status);
     else

@@ -16,7 +16,7 @@ cudaError_t launch_step_d3q27_f32(const void* fin, const void* gin, void* fout, 
     using R = typename S::R;
     const dim3 b = block_shape(geo.nx, block, 3);
     const auto c = make_coeffs<R, 27, 15>(hc);
-    if (index32(geo, 27))
+    if (step_index32(geo, 27, hc))
         step_d3q27_kernel<S, unsigned><<<grid_shape(geo, b), b, 0, st>>>(
             (const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo, c, status);
     else
@@ -38,7 +38,7 @@ static cudaError_t launch_tma_f32(const TmaMaps& tm, const void* fin, const void
     const int tiles_x = (geo.nx + kTmaTX - 1) / kTmaTX, tiles_y = (geo.ny + TY - 1) / TY;
     const int n_tiles = tiles_x * tiles_y * geo.nz;
     const dim3 block(kTmaTX * TY + 32, 1, 1);   // TY rows of consumers and one producer warp
-    auto kern = index32(geo, 27) ? step_d3q27_tma_kernel<S, unsigned, TY> : step_d3q27_tma_kernel<S, size_t, TY>;
+    auto kern = step_index32(geo, 27, hc) ? step_d3q27_tma_kernel<S, unsigned, TY> : step_d3q27_tma_kernel<S, size_t, TY>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmemBytes);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;

@@ -14,7 +14,7 @@ cudaError_t launch_step_d3q27_f64(const void* fin, const void* gin, void* fout, 
     using R = typename S::R;
     const dim3 b = block_shape(geo.nx, block, 3);
     const auto c = make_coeffs<R, 27, 15>(hc);
-    if (index32(geo, 27))
+    if (step_index32(geo, 27, hc))
         step_d3q27_kernel<S, unsigned><<<grid_shape(geo, b), b, 0, st>>>(
             (const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo, c, status);
     else
