@@ -45,7 +45,7 @@ enum lbm_status {
     LBM_ECUDA = 3,      /* a CUDA call failed; lbm_last_error has the CUDA message */
     LBM_EDIVERGED = 4,  /* a node saw a non-finite or non-positive density or a non-finite T */
     LBM_ETIMEOUT = 5,   /* a bounded device-side wait gave up (the kernel returned, no hang) */
-    LBM_ENOTSUP = 6     /* valid request that this build does not support */
+    LBM_ENOTSUP = 6     /* valid request that this library does not support */
 };
 
 /* Lattice pair, OR-ed with one storage precision. */
