@@ -99,4 +99,19 @@ __device__ __forceinline__ void uncentral_line(R& a, R& b, R& c, R u)
     c = h * (r2 + r1);
 }
 
+// uncentral_line with its outputs multiplied by 2^L, folded into the line's own halving.  Scaling
+// by a power of two is exact, so the outputs are bitwise 2^L times those of uncentral_line.
+template <int L, class R>
+__device__ __forceinline__ void uncentral_line_pow2(R& a, R& b, R& c, R u)
+{
+    constexpr double s = double(1ull << L);
+    const R k0 = a, k1 = b, k2 = c;
+    const R r1 = k1 + u * k0;
+    const R r2 = k2 + u * (k1 + r1);
+    const R h = R(0.5 * s);
+    a = h * (r2 - r1);
+    b = L == 0 ? k0 - r2 : R(s) * (k0 - r2);
+    c = h * (r2 + r1);
+}
+
 }  // namespace lbm

@@ -55,20 +55,28 @@ struct StoreF32 {
 struct StoreF16S {
     using T = __half;
     using R = float;
-    static constexpr float kScale = 1024.0f;
+    static constexpr int kScaleLog2 = 10;
+    static constexpr float kScale = 1024.0f;   // 2^kScaleLog2
     static constexpr float kInvScale = 1.0f / 1024.0f;
     __device__ static R load_dev(const T* p, size_t i, R)
     {
         return __half2float(ldg_pf256(p + i)) * kInvScale;
     }
     __device__ static void store_dev(T* p, size_t i, R dev, R) { p[i] = __float2half_rn(dev * kScale); }
+    // a deviation already multiplied by kScale
+    __device__ static void store_scaled(T* p, size_t i, R scaled) { p[i] = __float2half_rn(scaled); }
     // Two deviations converted together with stochastic rounding: each is rounded up or down to a
     // neighbouring FP16 value with probabilities that make the rounding unbiased, driven by the
     // caller's random bits (Blackwell's cvt.rs).  Returns (half of d0) | (half of d1) << 16.
     __device__ static unsigned pack_sr(R d0, R d1, unsigned rbits)
     {
+        return pack_sr_scaled(d0 * kScale, d1 * kScale, rbits);
+    }
+    // the same for deviations already multiplied by kScale
+    __device__ static unsigned pack_sr_scaled(R s0, R s1, unsigned rbits)
+    {
         unsigned h2;
-        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(h2) : "f"(d1 * kScale), "f"(d0 * kScale), "r"(rbits));
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(h2) : "f"(s1), "f"(s0), "r"(rbits));
         return h2;
     }
 };
@@ -231,13 +239,15 @@ __device__ __forceinline__ void static_for(F&& f)
 }
 
 // Store of one node's 2q deviations (flow planes then energy planes) through F16S storage with
-// stochastic rounding: consecutive values are converted in pairs.
-template <int QF, int QG, class Idx>
+// stochastic rounding: consecutive values are converted in pairs.  kScaled: df and dg are already
+// multiplied by the storage scale (the seed is still taken from the unscaled values' bits).
+template <int QF, int QG, class Idx, bool kScaled = false>
 __device__ __forceinline__ void store_node_f16s_sr(__half* __restrict__ fout, __half* __restrict__ gout,
                                                    Idx n, int i, const float* df, const float* dg)
 {
     constexpr int Q = QF + QG;
-    const unsigned seed = sr_seed((unsigned)i, df[0], dg[0]);
+    const float unscale = kScaled ? StoreF16S::kInvScale : 1.0f;
+    const unsigned seed = sr_seed((unsigned)i, df[0] * unscale, dg[0] * unscale);
     static_for<(Q + 1) / 2>([&](auto K) {
         constexpr int k = decltype(K)::value;
         constexpr int a0 = 2 * k, a1 = 2 * k + 1;
@@ -246,7 +256,8 @@ __device__ __forceinline__ void store_node_f16s_sr(__half* __restrict__ fout, __
         constexpr int f1 = a1 < QF ? a1 : 0, g1 = a1 < QF ? 0 : (a1 < Q ? a1 - QF : 0);
         const float v0 = a0 < QF ? df[f0] : dg[g0];
         const float v1 = a1 < Q ? (a1 < QF ? df[f1] : dg[g1]) : 0.0f;
-        const unsigned h2 = StoreF16S::pack_sr(v0, v1, sr_pair_bits<k>(seed));
+        const unsigned h2 = kScaled ? StoreF16S::pack_sr_scaled(v0, v1, sr_pair_bits<k>(seed))
+                                    : StoreF16S::pack_sr(v0, v1, sr_pair_bits<k>(seed));
         const __half h0 = __ushort_as_half((unsigned short)(h2 & 0xffffu));
         const __half h1 = __ushort_as_half((unsigned short)(h2 >> 16));
         if (a0 < QF) fout[(Idx)a0 * n + i] = h0;

@@ -241,7 +241,9 @@ __device__ __forceinline__ void central_from_xraw_d3q27(R p[3][3][3], R ux, R uy
         for (int a = 0; a < 3; ++a) central_line(p[0][b][a], p[1][b][a], p[2][b][a], uz);
 }
 
-template <class R>
+// Inverse transform; the populations come out multiplied by 2^L (L = 0 except for FP16 storage,
+// whose scale is folded in here instead of at the store).
+template <int L = 0, class R>
 __device__ __forceinline__ void from_central_d3q27(R p[3][3][3], R f[27], R ux, R uy, R uz)
 {
 #pragma unroll
@@ -255,7 +257,7 @@ __device__ __forceinline__ void from_central_d3q27(R p[3][3][3], R f[27], R ux, 
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) uncentral_line(p[k][j][0], p[k][j][1], p[k][j][2], ux);
+        for (int j = 0; j < 3; ++j) uncentral_line_pow2<L>(p[k][j][0], p[k][j][1], p[k][j][2], ux);
     static_for<27>([&](auto A) {
         constexpr int a = decltype(A)::value;
         f[a] = p[e27(a, 2) + 1][e27(a, 1) + 1][e27(a, 0) + 1];
@@ -311,8 +313,9 @@ __device__ __forceinline__ G15Raw<R> raw_g_d3q15(const R g[15])
 // or option B, in deviation form.  `d` holds the Step-1 raw moments of the deviations
 // gamma = g - w T_o, and T = T_o + d.r000.  The rest state w T_o has the raw moments
 // T_o (1, 1/3, 1/3, 1/3, 1/9) on (000, 200, 020, 002, 220) and none else: they are added before
-// Step 2 and removed again after Step 4, so Step 5 writes the post-collision deviations to gd.
-template <class R>
+// Step 2 and removed again after Step 4, so Step 5 writes the post-collision deviations to gd,
+// multiplied by 2^L (exactly; L = 10 folds the FP16 storage scale into Step 5's own weights).
+template <int L = 0, class R>
 __device__ __forceinline__ void collide_g_d3q15(const G15Raw<R>& d, R T_ref, R T, R ux, R uy, R uz,
                                                 const R om[15], int gopt, R gd[15])
 {
@@ -406,14 +409,17 @@ __device__ __forceinline__ void collide_g_d3q15(const G15Raw<R>& d, R T_ref, R T
     const R Sx = q200d - q220d, Dx = q100 - q120;
     const R Sy = q020d - q220d, Dy = q010 - q012;
     const R Sz = q002d - q220d, Dz = q001 - q201;
-    gd[0] = q000d - q200d - q020d - q002d + R(2) * q220d;
-    gd[1] = R(0.5) * (Sx + Dx);
-    gd[2] = R(0.5) * (Sx - Dx);
-    gd[3] = R(0.5) * (Sy + Dy);
-    gd[4] = R(0.5) * (Sy - Dy);
-    gd[5] = R(0.5) * (Sz + Dz);
-    gd[6] = R(0.5) * (Sz - Dz);
-    const R e = R(0.125);
+    constexpr double s = double(1ull << L);
+    const R g0 = q000d - q200d - q020d - q002d + R(2) * q220d;
+    gd[0] = L == 0 ? g0 : R(s) * g0;
+    const R hs = R(0.5 * s);
+    gd[1] = hs * (Sx + Dx);
+    gd[2] = hs * (Sx - Dx);
+    gd[3] = hs * (Sy + Dy);
+    gd[4] = hs * (Sy - Dy);
+    gd[5] = hs * (Sz + Dz);
+    gd[6] = hs * (Sz - Dz);
+    const R e = R(0.125 * s);
     // z split
     const R P_s = q220d + q201, M_s = q220d - q201;   // sum part for z+ / z-
     const R P_y = q012 + q011, M_y = q012 - q011;
@@ -533,15 +539,27 @@ __device__ __forceinline__ void collide_store_d3q27(typename S::R f[27], typenam
     if constexpr (!kLineSums) xraw_d3q27(f, p);
     central_from_xraw_d3q27(p, ux, uy, uz);
     relax_f_d3q27(p, drho, irho, ux, uy, uz, Fx, Fy, Fz, c);
-    from_central_d3q27(p, f, ux, uy, uz);
+    // FP16 storage keeps deviations times 2^10: both collisions return them already scaled
+    constexpr bool kF16 = std::is_same<S, StoreF16S>::value;
+    constexpr int kL = kF16 ? StoreF16S::kScaleLog2 : 0;
+    from_central_d3q27<kL>(p, f, ux, uy, uz);
     // energy collision on the deviations: g receives the post-collision gamma
-    collide_g_d3q15(gr, c.T_ref, T, ux, uy, uz, c.om_g, c.gopt, g);
+    collide_g_d3q15<kL>(gr, c.T_ref, T, ux, uy, uz, c.om_g, c.gopt, g);
 
-    if constexpr (std::is_same<S, StoreF16S>::value) {
+    if constexpr (kF16) {
         if (c.fp16_sr) {
-            store_node_f16s_sr<27, 15, Idx>(fout, gout, (Idx)geo.n, i, f, g);
-            return;
+            store_node_f16s_sr<27, 15, Idx, true>(fout, gout, (Idx)geo.n, i, f, g);
+        } else {
+            static_for<27>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                StoreF16S::store_scaled(fout, (Idx)a * geo.n + i, f[a]);
+            });
+            static_for<15>([&](auto B) {
+                constexpr int b = decltype(B)::value;
+                StoreF16S::store_scaled(gout, (Idx)b * geo.n + i, g[b]);
+            });
         }
+        return;
     }
     static_for<27>([&](auto A) {
         constexpr int a = decltype(A)::value;
