@@ -66,3 +66,20 @@ def test_single_rank_helpers_are_identities():
     assert bench.reduce_max(3.5, 1) == 3.5
     bench.barrier(1)
     assert bench.job_mlups(100, 10, 1, 2.0) == pytest.approx(5e-4)
+
+
+@pytest.mark.parametrize("argv", [["--batch-launch", "64x1x160"],
+                                  ["--only", "batched", "--batch-launch", "64x1"],
+                                  ["--warmup", "2"]])
+def test_bench_rejects_bad_arguments(argv):
+    """A fixed batch launch needs --only batched and three sizes; fewer than 3 warm-up steps is refused."""
+    with pytest.raises(SystemExit) as e:
+        bench.main(argv)
+    assert e.value.code == 2
+
+
+def test_fp64_roofline_uses_the_counted_operations():
+    r = bench.fp64_alu_roofline(500.0, "d3q27")
+    assert r["bound"] == "alu"
+    assert r["achieved"] == pytest.approx(500.0 * bench.FP64_OPS_PER_NODE["d3q27"] / 1e3, rel=1e-3)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], rel=1e-3)
