@@ -107,6 +107,22 @@ class ClockSampler:
                 self.proc.kill()
             self.thread.join(timeout=2)
 
+    def median_sm_mhz(self, start, end):
+        """Median SM clock of the samples taken between two datetime.now() marks, or None."""
+        from datetime import datetime
+        sm = []
+        for line in list(self.lines):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                if start <= ts <= end:
+                    sm.append(float(parts[2]))
+            except ValueError:
+                continue
+        return statistics.median(sm) if sm else None
+
     def summary(self):
         from datetime import datetime
         sm, mx, reasons, power = [], None, set(), []
@@ -220,6 +236,11 @@ def run_gpu(args):
         ev[2].record(stream)
         torch.cuda.synchronize()
         clocks.mark(t_start, datetime.now())
+        # the other forms run while the sampler still records, so the FP64 forms are set
+        # against the SM clock seen while they ran
+        forms = []
+        if world == 1 and not args.no_forms:
+            forms = measure_forms(L, torch, stream, args, clocks)
     barrier(world)
     lat.sync()
     t_total = ev[0].elapsed_time(ev[2]) / 1e3
@@ -243,9 +264,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t_e2e = reduce_max(time.perf_counter() - t0, world)
 
-    forms, adjoint, batched, nu_acc = [], None, None, None
+    adjoint, batched, nu_acc = None, None, None
     if world == 1 and not args.no_forms:
-        forms = measure_forms(L, torch, stream, args)
         nu_acc = measure_nu_accuracy(L, stream)
         batched = measure_batched(L, torch, stream)
         adjoint = measure_adjoint(L, torch, stream)
@@ -309,42 +329,104 @@ def run_gpu(args):
         "nusselt": {"hot_mean": nu_hot[0], "cold_mean": nu_cold[0],
                     "after_steps": args.warmup + args.steps},
     }
+    cpu = None if args.no_cpu_baseline else cpu_baseline(seconds=args.cpu_seconds)
+    return append_secondary(line, forms, nu_acc, batched, adjoint, cpu)
+
+
+def append_secondary(line, forms, nu_acc, batched, adjoint, cpu):
+    """Add the secondary measurements to the bench line: the detailed records first, the compact
+    per-form table and the accuracy summary last, so that a reader who keeps only the end of the
+    line still sees every form's figures."""
     if forms:
-        line["per_form"] = forms
+        line["per_form_detail"] = forms
     if nu_acc:
-        line["nu_accuracy"] = nu_acc
+        line["nu_accuracy_detail"] = nu_acc
     if batched:
         line["batched"] = batched
     if adjoint:
         line["adjoint"] = adjoint
     line["paper_context"] = PAPER_CONTEXT
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
+    if cpu:
+        line["cpu_baseline"] = cpu
+    if nu_acc:
+        line["nu_accuracy"] = compact_nu_accuracy(nu_acc)
+    if forms or batched or adjoint:
+        line["per_form"] = compact_forms(line, forms, batched, adjoint)
     return line
 
 
-# FP64 lane operations per node update of the FP64 steps (ncu counts in
-# profiles/flops_step_d3q27.md) and GB300's FP64 pipe rate: 2 lane operations per SM per clock.
+FORM_BOUND = {"fp32": "hbm", "fp16s": "issue", "fp64": "fp64 alu"}
+
+
+def compact_forms(line, forms, batched, adjoint):
+    """One short record per measured form: the headline, the other lattice / precision forms,
+    the batched ensemble and the adjoint ratio."""
+    r = line["roofline"]
+    cfg = line["config"]
+    out = [{"form": f"{'3D' if cfg['nz'] > 1 else '2D'} {line['dtype']} (headline)",
+            "box": f"{cfg['nx']}x{cfg['ny']}x{cfg['nz']}", "mlups": line["value"],
+            "gbs": r["achieved"], "hbm_frac": r["frac"], "bound": r["bound"]}]
+    for f in forms:
+        rec = {"form": f"{'3D' if f['lattice'].startswith('D3') else '2D'} {f['precision']}"
+                       + (" option B" if f["g_attractors"] == "option B" else ""),
+               "box": "x".join(str(v) for v in f["box"]), "mlups": f["mlups"], "gbs": f["gbs"],
+               "hbm_frac": f["hbm_frac"], "bound": FORM_BOUND[f["precision"]]}
+        if "roofline" in f:
+            rec["alu_frac"] = f["roofline"]["frac"]
+        if f.get("l2_resident"):
+            rec["note"] = "one step's state fits in L2: not an HBM figure"
+        out.append(rec)
+    if batched:
+        out.append({"form": "2D fp32 batched ensemble", "box": f"{batched['nodes']} nodes",
+                    "mlups": batched["mlups"], "gbs": batched["gbs"], "hbm_frac": batched["hbm_frac"],
+                    "bound": "hbm", "speedup_vs_unbatched": batched["speedup_vs_unbatched"]})
+    if adjoint:
+        out.append({"form": "2D adjoint 256x256 (double-float VJP)",
+                    "adjoint_ms_per_step": adjoint["adjoint_ms_per_step"],
+                    "forward_ms_per_step": adjoint["forward_ms_per_step"],
+                    "adjoint_over_forward": adjoint["adjoint_over_forward"]})
+    return out
+
+
+def compact_nu_accuracy(nu_acc):
+    """Mean hot-wall Nu of FP64 and the relative deviation of the FP32 and FP16S forms."""
+    return [{"case": a["case"].split(",")[0] + ", " + a["case"].split(",")[1].strip(),
+             "nu_fp64": round(a["nu_hot_mean"]["fp64"], 6),
+             "fp32_rel": float(f"{a['rel_vs_fp64']['fp32']:.3g}"),
+             "fp16s_rel": float(f"{a['rel_vs_fp64']['fp16s']:.3g}")} for a in nu_acc]
+
+
+# FP64 lane operations per node update of the FP64 steps (ncu instruction counts of the FP64
+# kernels, committed with the profiles) and GB300's FP64 pipe rate: 2 lane operations per SM per
+# clock.
 FP64_OPS_PER_NODE = {"d3q27": 973.8, "d2q9": 340.6}
 FP64_LANE_OPS_PER_SM_CLK = 2
 
 
-def fp64_alu_roofline(mlups: float, lattice: str = "d3q27", sms: int = 152, clock_ghz: float = 2.07):
+def fp64_alu_roofline(mlups: float, lattice: str = "d3q27", sms: int = 152, clock_ghz: float = 2.07,
+                      clock_kind: str = "nominal maximum"):
+    """The FP64 form against the FP64 pipe: sms and clock_ghz are the device's SM count and the
+    SM clock sampled while the form ran (the nominal maximum when no sample was taken)."""
     peak = sms * FP64_LANE_OPS_PER_SM_CLK * clock_ghz              # G lane-ops / s
     achieved = mlups * 1e6 * FP64_OPS_PER_NODE[lattice] / 1e9
     return {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1),
             "unit": "G FP64 lane-ops/s", "frac": round(achieved / peak, 4),
-            "peak_kind": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz"}
+            "peak_kind": f"derived: {sms} SMs x {FP64_LANE_OPS_PER_SM_CLK} FP64 lanes/clk x "
+                         f"{clock_ghz:.3f} GHz ({clock_kind})"}
 
 
-def measure_forms(L, torch, stream, args):
-    """MLUPS and HBM fraction of the other lattice / precision forms on the same GPU."""
+def measure_forms(L, torch, stream, args, clocks=None):
+    """MLUPS and HBM fraction of the other lattice / precision forms on the same GPU.  The FP64
+    forms are also set against the FP64 pipe of this device (its SM count, and the median SM clock
+    sampled while the form ran)."""
+    from datetime import datetime
     out = []
     peak, _ = hbm_peak()
-    cases = [("d3q27", 256, 256, 256, "fp64", L.Walls.cavity(3), 1e6, 20, 0),
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    cases = [("d3q27", 256, 256, 256, "fp64", L.Walls.cavity(3), 1e6, 40, 0),
              ("d3q27", 256, 256, 256, "fp16s", L.Walls.cavity(3), 1e6, 50, 0),
              ("d3q27", 256, 256, 256, "fp32", L.Walls.cavity(3), 1e6, 50, 1),
-             ("d2q9", 1024, 512, 1, "fp64", L.Walls.rayleigh_benard(seed=1), 1e8, 200, 0),
+             ("d2q9", 1024, 512, 1, "fp64", L.Walls.rayleigh_benard(seed=1), 1e8, 2000, 0),
              ("d2q9", 1024, 512, 1, "fp32", L.Walls.rayleigh_benard(seed=1), 1e8, 400, 0),
              ("d2q9", 1024, 512, 1, "fp16s", L.Walls.rayleigh_benard(seed=1), 1e8, 400, 0)]
     for lat_name, nx, ny, nz, prec, walls, Ra, k, gopt in cases:
@@ -353,10 +435,12 @@ def measure_forms(L, torch, stream, args):
         lat.step(5)
         lat.sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_a = datetime.now()
         e0.record(stream)
         lat.step(k)
         e1.record(stream)
         torch.cuda.synchronize()
+        t_b = datetime.now()
         lat.sync()
         s = e0.elapsed_time(e1) / 1e3 / k
         bpn = lat.info().bytes_per_node_update
@@ -365,9 +449,13 @@ def measure_forms(L, torch, stream, args):
                "precision": prec, "box": [nx, ny, nz], "mlups": round(lat.n / s / 1e6, 1),
                "ms_per_step": round(s * 1e3, 4), "gbs": round(gbs, 1),
                "hbm_frac": round(gbs / peak, 4), "steps": k,
-               "g_attractors": "option B" if gopt else "option A"}
+               "g_attractors": "option B" if gopt else "option A",
+               "l2_resident": bpn / 2 * lat.n < 129e6}
         if prec == "fp64":
-            rec["roofline"] = fp64_alu_roofline(lat.n / s / 1e6, lat_name)
+            mhz = clocks.median_sm_mhz(t_a, t_b) if clocks is not None else None
+            rec["roofline"] = (fp64_alu_roofline(lat.n / s / 1e6, lat_name, sms, mhz / 1e3,
+                                                 "median SM clock sampled during the form")
+                               if mhz else fp64_alu_roofline(lat.n / s / 1e6, lat_name, sms))
         out.append(rec)
         lat.close()
     return out
@@ -397,7 +485,7 @@ def measure_nu_accuracy(L, stream):
 def measure_batched(L, torch, stream, steps: int = 2000, unbatched_steps: int = 256,
                     compare: bool = True, launch=None):
     """The ensemble workload: 64 independent square cavities (sides 64..512, Ra log-uniform in
-    [1e3, 1e7], Pr uniform in [0.71, 7], seeded), FP32, one autotuned persistent launch per
+    [1e3, 1e7], Pr uniform in [0.71, 7], seeded), FP32, one autotuned launch per
     step replayed from CUDA graphs.  Compared with the same members advanced one handle at a
     time (each with its own CUDA graphs), and, for a few members, the wall Nusselt number
     against FP64 unbatched runs of the same length."""
@@ -464,7 +552,7 @@ def measure_batched(L, torch, stream, steps: int = 2000, unbatched_steps: int = 
     b.close()
     gbs = bpn * nodes / t / 1e9
     return {"workload": "64 independent 2D cavities, sides drawn from {64,...,512}, Ra log-uniform "
-                        "[1e3, 1e7], Pr uniform [0.71, 7], FP32, one persistent launch per step "
+                        "[1e3, 1e7], Pr uniform [0.71, 7], FP32, one autotuned launch per step "
                         "under CUDA graphs",
             "nodes": nodes, "mlups": round(nodes / t / 1e6, 1), "ms_per_step": round(t * 1e3, 5),
             "gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4), "steps": steps,

@@ -10,8 +10,8 @@
  *
  * Conventions used by every entry point:
  *  - Return value: LBM_OK (0) or one of the lbm_status codes; nothing traps, no exception crosses
- *    the ABI.  lbm_last_error(h) describes the most recent failure on h (or of lbm_create when
- *    h is NULL).
+ *    the ABI.  lbm_last_error(h) describes the most recent failure on h (or, when h is NULL,
+ *    of a call without a handle on the calling thread).
  *  - Node index i = x + nx * (y + ny * z), x fastest.  Population arrays are [q][nz][ny][nx] in
  *    the paper's link order (D2Q9 Eqs. ex, ey; D3Q27 Sec. 5.2; D3Q15 Sec. 5.4).
  *  - Faces are numbered 0..5 = -x, +x, -y, +y, -z, +z.  2D boxes have nz = 1 and ignore the z faces.
@@ -188,7 +188,9 @@ LBM_API int lbm_nusselt(lbm_handle h, int face, double* mean, double* nu_max, do
 LBM_API int lbm_nusselt_profile(lbm_handle h, int face, double* nu, long n, int device_ptrs);
 
 /* Per-node wall temperature of a fixed-T face (n = face nodes, tangential order as above, host
- * pointer); T_w = NULL returns the face to its uniform T_wall.  Errors: LBM_EINVAL. */
+ * pointer); T_w = NULL returns the face to its uniform T_wall.  The profile enters the
+ * half-way anti-bounce-back of Sec. 6.1, g_abar = -g~_a + 2 w_a T_w(j), on every link that crosses
+ * the face at node j, and the wall value of the Nusselt derivative there.  Errors: LBM_EINVAL. */
 LBM_API int lbm_set_wall_profile(lbm_handle h, int face, const double* T_w, long n);
 
 /*
@@ -226,6 +228,8 @@ LBM_API int lbm_set_populations(lbm_handle h, const double* f, const double* g, 
 LBM_API int lbm_get_state(lbm_handle h, void* buf, size_t bytes);
 LBM_API int lbm_set_state(lbm_handle h, const void* buf, size_t bytes);
 
+/* The message of the most recent failure on h; with h = NULL, that of the most recent failed
+ * call without a handle (lbm_create, lbm_nusselt_static) on the calling thread. */
 LBM_API const char* lbm_last_error(lbm_handle h);
 LBM_API const char* lbm_status_string(int status);
 
@@ -261,14 +265,20 @@ LBM_API int lbm_probe_bounded_wait(double seconds, int* timed_out);
  *  result     device pointer to 5 doubles: mean Nu, max Nu, its tangential node index, min Nu,
  *             its index (indices stored as doubles), with the definitions of lbm_nusselt.
  *  stream     cudaStream_t to run on (NULL = legacy stream); the call returns without waiting.
+ * Wall temperatures are uniform per face: T_wall[f] is used at every node of face f, both in the
+ * anti-bounce-back of the pulled populations and as T_w of the derivative.  A per-node profile set
+ * on a handle with lbm_set_wall_profile is not seen here; for such a state use lbm_nusselt.
  * Errors: LBM_EINVAL for a bad argument, including a face with more than
  * LBM_NUSSELT_STATIC_MAX_FACE_NODES nodes (the scratch array has room for that many);
- * LBM_ECUDA if a CUDA call fails.
- * The first call on each device performs a one-time set-up with that device current: it looks
- * up the device address of the scratch array.  Make that first call before any stream capture
- * begins.  Every call uses the same scratch array, which keeps the last call's contents: calls
- * that may run at the same time on the GPU (on unordered streams, or from several host threads)
- * race and give wrong results, so order them on one stream.
+ * LBM_ECUDA if a CUDA call fails.  lbm_last_error(NULL), on the calling thread, gives the reason.
+ * Set-up: the first call on each device looks up the device address of the scratch array with
+ * that device current (this also creates the device's primary context if there is none yet).
+ * The lookup is repeated when the device's current context has changed since, for instance after
+ * cudaDeviceReset, which reloads the library's device code in a new context.  Make the first call
+ * on a device, and the first call after such a reset, before any stream capture begins.  Every
+ * call uses the same scratch array, which keeps the last call's contents: calls that may run at
+ * the same time on the GPU (on unordered streams, or from several host threads) race and give
+ * wrong results, so order them on one stream.
  */
 #define LBM_NUSSELT_STATIC_MAX_FACE_NODES 1048576
 LBM_API int lbm_nusselt_static(int lattice, int nx, int ny, int nz, const int face_kind[6],
@@ -280,9 +290,12 @@ LBM_API int lbm_nusselt_static(int lattice, int nx, int ny, int nz, const int fa
  * Rayleigh and Prandtl number (Sec. 6.1: Ra = 10^3 .. 10^10 at Pr = 0.71 and grids up to 512^2;
  * Sec. 7: sweeps of Ma, resolution and Pr = 0.1 .. 5).  A batch holds such members (D2Q9 flow and
  * energy lattices, one storage precision) and advances all of them by one time step with ONE
- * persistent kernel launch: the members' populations are concatenated in the same [q][y][x]
- * layout, the launch's (SM count x CTAs per SM) blocks stride over the list of every member's
- * tiles, and each member keeps its own geometry, relaxation rates and divergence flag.  Every
+ * kernel launch: the members' populations are concatenated in the same [q][y][x] layout, and the
+ * list of every member's tiles is split into equal contiguous shares, one per block.  The grid
+ * is (SM count x blocks per SM) with blocks per SM chosen by lbm_batch_set_launch or the tuner,
+ * usually several times what the SMs hold at once (an oversubscribed grid), so the hardware block
+ * scheduler balances the uneven members.  Each member keeps its own geometry, relaxation rates
+ * and divergence flag.  Every
  * member's step is the same arithmetic as lbm_step on a handle created with the same arguments,
  * so the two give bitwise identical populations.
  * Batch handles follow the conventions of lbm_handle (allocator hook, stream, not thread-safe).

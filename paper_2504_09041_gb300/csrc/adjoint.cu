@@ -25,6 +25,14 @@ static cudaError_t run_adjoint(const void* f_prev, const void* g_prev, const voi
 {
     using T = typename S::T;
     using R = typename S::R;
+    if (hc.adj_sync) {
+        const dim3 b(hc.adj_sync == 2 ? 128 : 64, hc.adj_sync == 2 ? 2 : 4, 1);
+        const dim3 grid((geo.nx + b.x - 1) / b.x, (geo.ny + b.y - 1) / b.y, 1);
+        adjoint_step_d2q9_kernel<S, RT, true><<<grid, b, 0, st>>>(
+            (const T*)f_prev, (const T*)g_prev, (const RT*)mu_in, (RT*)mu_out, geo,
+            make_coeffs<R, 9, 9>(hc), make_coeffs<RT, 9, 9>(hc), design_face, grad);
+        return cudaGetLastError();
+    }
     const dim3 b(64, 2, 1);
     const dim3 grid((geo.nx + b.x - 1) / b.x, (geo.ny + b.y - 1) / b.y, 1);
     adjoint_step_d2q9_kernel<S, RT><<<grid, b, 0, st>>>(

@@ -366,7 +366,7 @@ __device__ __forceinline__ void collide_forward_tape(const RF pf[9], const RF pg
 
 // Vector-Jacobian product of the node collision at the forward values tp: adjoints of the
 // post-collision deviations (lf, lg) -> adjoints of the pulled deviations (mf, mg), in RT.
-template <class RT>
+template <class RT, bool kSync = false>
 __device__ __forceinline__ void collide_vjp_d2q9(const CollideTape<RT>& tp, const RT lf[9],
                                                  const RT lg[9], const Coeffs2D<RT>& c, RT mf[9],
                                                  RT mg[9])
@@ -386,6 +386,7 @@ __device__ __forceinline__ void collide_vjp_d2q9(const CollideTape<RT>& tp, cons
         dTb += Tfb;
         sweeps_vjp(tp.gX, tp.gN, Nb, ux, uy, mg, uxb, uyb);
     }
+    if constexpr (kSync) __syncthreads();
     // flow chain on deviations
     {
         RT Tb[3][3], Db[3][3];
@@ -422,8 +423,13 @@ __device__ __forceinline__ int first_fixed_face(const NodeWalls<R>& w)
 
 // One adjoint step at every node (see the file comment).  mu_in = mu_{k+1}, mu_out = mu_k, both
 // [18][n] in RT (f links 0..8, then g links 0..8); f_prev, g_prev = s_{k-1} in storage format.
-template <class S, class RT>
-__global__ void __launch_bounds__(128)
+//
+// kSync: the block's warps pass a barrier between the phases of the node's work (gather, forward
+// tape, energy VJP, flow VJP), so that they run the same stretch of the long unrolled code at the
+// same time and share its instruction fetches.  Threads beyond the box then compute on a clamped
+// node and store nothing, so every thread reaches every barrier.
+template <class S, class RT, bool kSync = false>
+__global__ void __launch_bounds__(kSync ? 256 : 128, kSync ? 2 : 1)
     adjoint_step_d2q9_kernel(const typename S::T* __restrict__ f_prev,
                              const typename S::T* __restrict__ g_prev,
                              const RT* __restrict__ mu_in, RT* __restrict__ mu_out, Geometry geo,
@@ -431,9 +437,12 @@ __global__ void __launch_bounds__(128)
                              double* __restrict__ grad)
 {
     using R = typename S::R;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= geo.nx || y >= geo.ny) return;
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool active = x < geo.nx && y < geo.ny;
+    if (!kSync && !active) return;
+    x = min(x, geo.nx - 1);
+    y = min(y, geo.ny - 1);
     const int i = x + geo.nx * y;
     const size_t n = geo.n;
     const NodeWalls<R> w = node_walls<R>(geo, x, y, 0, 2);
@@ -456,13 +465,16 @@ __global__ void __launch_bounds__(128)
         }
     });
 
+    if constexpr (kSync) __syncthreads();
     // forward pull of p_k from s_{k-1}
     R fr[9], gr[9];
     pull_d2q9<S, size_t>(f_prev, g_prev, geo, w, i, cr.T_ref, fr, gr);
     CollideTape<RT> tape;
     collide_forward_tape(fr, gr, cr, tape);
+    if constexpr (kSync) __syncthreads();
     RT mf[9], mg[9];
-    collide_vjp_d2q9(tape, lf, lg, c, mf, mg);
+    collide_vjp_d2q9<RT, kSync>(tape, lf, lg, c, mf, mg);
+    if (!active) return;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
         mu_out[(size_t)a * n + i] = mf[a];

@@ -181,6 +181,17 @@ const char* lbm_last_error(lbm_handle h)
 
 namespace lbm {
 
+int fail_no_handle(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_create_error = buf;
+    return code;
+}
+
 void current_allocator(lbm_alloc_fn* a, lbm_free_fn* f, void** ctx)
 {
     *a = g_alloc;
@@ -443,6 +454,18 @@ int lbm_set_param(lbm_handle h, const char* key, double v)
         h->hc.index64 = (int)v;
         return LBM_OK;
     }
+    if (k == "adjoint_sync") {
+        if (!(v == 0.0 || v == 1.0 || v == 2.0)) return fail(h, LBM_EINVAL, "adjoint_sync must be 0, 1 or 2");
+        h->hc.adj_sync = (int)v;
+        return LBM_OK;
+    }
+    if (k == "l2_prefetch") {
+        const int v_i = (int)v;
+        if (v != (double)v_i || v_i < 0 || v_i > (1 << 24))
+            return fail(h, LBM_EINVAL, "l2_prefetch must be an integer in [0, 2^24] (blocks ahead)");
+        h->hc.l2_pf = v_i;
+        return LBM_OK;
+    }
     if (k == "fp16_stochastic") {
         if (!(v == 0.0 || v == 1.0)) return fail(h, LBM_EINVAL, "fp16_stochastic must be 0 or 1");
         h->hc.fp16_sr = (int)v;
@@ -550,6 +573,7 @@ int lbm_step(lbm_handle h, long n)
 {
     if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
     if (n < 0) return fail(h, LBM_EINVAL, "negative step count %ld", n);
+    const lbm::NvtxRange range("lbm_step");
     // whole graphs of graph_steps steps, then single launches
     while (h->graph_steps > 0 && n >= h->graph_steps) {
         const int par = h->cur;
@@ -698,6 +722,7 @@ int lbm_adjoint_step(lbm_handle h, long n_steps, int objective_face, int design_
     const int ext[2] = {h->nx, h->ny};
     if (ext[objective_face / 2] < 3) return fail(h, LBM_EINVAL, "fewer than three node layers normal to the objective face");
     if (n != face_nodes(h, design_face)) return fail(h, LBM_EINVAL, "design face %d has %ld nodes, not %ld", design_face, face_nodes(h, design_face), n);
+    const lbm::NvtxRange range("lbm_adjoint_step");
 
     const size_t sb = lbm::storage_bytes(h->prec);
     const size_t fb = (size_t)h->qf * h->geo.n * sb, gb = (size_t)h->qg * h->geo.n * sb;

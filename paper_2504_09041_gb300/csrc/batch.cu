@@ -1,12 +1,14 @@
-// batch.cu -- many independent 2D cavities (D2Q9 flow + D2Q9 energy) advanced by one persistent
+// batch.cu -- many independent 2D cavities (D2Q9 flow + D2Q9 energy) advanced by one kernel
 // launch per time step.
 //
 // The members' populations are concatenated in two buffers (f and g, each with its own A/B copy);
 // a device table holds every member's geometry, relaxation rates and buffer offset, and the
-// first index of its tiles.  The launch has (SM count x CTAs per SM) blocks, all resident at
-// once; block b takes an equal contiguous share of the global tile list, stages the owning
-// member's table entry in shared memory (again only where its share crosses into the next
-// member) and runs the same node step as the single-box kernel on one node per thread.  The
+// first index of its tiles.  The launch has (SM count x CTAs per SM) blocks, usually more than
+// the SMs hold at once, so the hardware block scheduler balances the shares (an oversubscribed
+// grid, not a persistent one).  Block b takes an equal contiguous share of the global tile list,
+// stages the owning member's table entry in shared memory (again only where its share crosses
+// into the next member) and runs the same node step as the single-box kernel on one node per
+// thread.  The
 // tile shape and CTAs per SM come from lbm_batch_set_launch or from the autotuner
 // lbm_batch_tune; the time loop replays CUDA graphs like lbm_step.
 #include <algorithm>
@@ -404,6 +406,7 @@ int lbm_batch_step(lbm_batch b, long n)
 {
     if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
     if (n < 0) return bfail(b, LBM_EINVAL, "negative step count");
+    const lbm::NvtxRange range("lbm_batch_step");
     while (b->graph_steps > 0 && n >= b->graph_steps) {
         const int par = b->cur;
         if (!b->graph[par] || b->graph_gen[par] != b->gen) {

@@ -5,11 +5,23 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbm_common.cuh"
 #include "../../include/lbm.h"
 #include <string>
 
 namespace lbm {
+
+// A named NVTX range on the calling thread's timeline for the duration of a library call
+// (lbm_step, lbm_batch_step, lbm_adjoint_step): profilers that record NVTX show it above the
+// kernels the call queued; without such a tool attached it costs two calls into a stub.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 enum Prec { kF64 = 0, kF32 = 1, kF16S = 2 };
 
@@ -22,6 +34,8 @@ struct HostCoeffs {
     int gopt;   // energy attractors of orders 3-4: 0 = option A, 1 = option B
     int fp16_sr;   // F16S storage: stochastic (1) or nearest (0) rounding of stored deviations
     int index64;   // 1: the step uses 64-bit element offsets even where 32-bit ones suffice
+    int l2_pf;     // 3D step: blocks ahead whose input rows each block prefetches into L2 (0: off)
+    int adj_sync;  // adjoint step: 0 = 64x2 blocks; 1 = 64x4, 2 = 128x2 blocks with phase barriers
 };
 
 size_t storage_bytes(int prec);
@@ -35,6 +49,9 @@ struct BoxPlan {
 };
 int plan_box(int lattice, int nx, int ny, int nz, double Ra, double Pr, double Ma, const lbm_bc* bc,
              BoxPlan* P, std::string* err);
+// Records the message of a failed call that has no handle (lbm_create, lbm_nusselt_static); lbm_last_error(NULL)
+// returns it on the calling thread.  Returns code.
+int fail_no_handle(int code, const char* fmt, ...);
 // The process-wide device allocator hooks of lbm_set_allocator.
 void current_allocator(lbm_alloc_fn* a, lbm_free_fn* f, void** ctx);
 
@@ -123,6 +140,7 @@ inline Coeffs<R, QF, QG> make_coeffs(const HostCoeffs& h)
     c.gaxis = h.gaxis;
     c.gopt = h.gopt;
     c.fp16_sr = h.fp16_sr;
+    c.l2_pf = h.l2_pf;
     return c;
 }
 

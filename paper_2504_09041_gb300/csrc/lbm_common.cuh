@@ -132,6 +132,7 @@ struct Coeffs {
     int gaxis;    // 0, 1, 2
     int gopt;     // energy attractors of orders 3-4: 0 = option A, 1 = option B (renormalized)
     int fp16_sr;  // F16S storage: 1 = stochastic rounding of the stored deviations, 0 = nearest
+    int l2_pf;    // 3D step: L2 prefetch of the input rows of the block this many blocks ahead (0: off)
 };
 
 // Per-thread wall bookkeeping for the pull.  For an axis, "m" is a link whose source lies at

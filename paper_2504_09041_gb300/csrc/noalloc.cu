@@ -148,34 +148,72 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// Device address of g_scratch, looked up once per device with that device current.
-std::mutex g_mu;
-double* g_addr[64] = {nullptr};
+// Device address of g_scratch in the current context.  The runtime loads this library's module
+// once per context, so the address is looked up (cudaGetSymbolAddress, with the device current)
+// on the first call on each device and again whenever that device's current context is a
+// different one: after cudaDeviceReset destroyed the primary context and a later call created a
+// new one, the module is reloaded and the array may sit elsewhere.  Contexts are told apart by
+// the driver's context ID, which is never reused within a process.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
 
-cudaError_t scratch_address(double** out)
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    double* addr;
+};
+
+std::mutex g_mu;
+ScratchSlot g_slot[64] = {};
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+
+// ID of the calling thread's current context, or false when there is none.
+bool current_context_id(unsigned long long* id)
+{
+    CUcontext ctx = nullptr;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return false;
+    return g_ctx_id(ctx, id) == CUDA_SUCCESS;
+}
+
+int scratch_address(double** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (e != cudaSuccess) return fail_no_handle(LBM_ECUDA, "lbm_nusselt_static: cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64) return fail_no_handle(LBM_ECUDA, "lbm_nusselt_static: device ordinal %d above 63", dev);
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev] = static_cast<double*>(p);
+    if (!g_ctx_current || !g_ctx_id) {
+        void* p0 = nullptr;
+        void* p1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p0, 12000, cudaEnableDefault, &q0) != cudaSuccess ||
+            q0 != cudaDriverEntryPointSuccess || !p0 ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &p1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || !p1)
+            return fail_no_handle(LBM_ECUDA, "lbm_nusselt_static: cuCtxGetCurrent / cuCtxGetId are not available from the driver");
+        g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(p0);
+        g_ctx_id = reinterpret_cast<CtxGetIdFn>(p1);
     }
-    *out = g_addr[dev];
-    return cudaSuccess;
+    unsigned long long id = 0;
+    if (g_slot[dev].addr && current_context_id(&id) && id == g_slot[dev].ctx_id) {
+        *out = g_slot[dev].addr;
+        return LBM_OK;
+    }
+    // set-up: this also creates and makes current the device's primary context if needed
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return fail_no_handle(LBM_ECUDA, "lbm_nusselt_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    if (!current_context_id(&id)) return fail_no_handle(LBM_ECUDA, "lbm_nusselt_static: no current CUDA context");
+    g_slot[dev] = ScratchSlot{id, static_cast<double*>(p)};
+    *out = g_slot[dev].addr;
+    return LBM_OK;
 }
-
-int err(int code, const char*)
-{
-    return code;
-}
+#undef err
 
 }  // namespace
 }  // namespace lbm
+
+#define err(code, ...) lbm::fail_no_handle(code, "lbm_nusselt_static: " __VA_ARGS__)
 
 extern "C" int lbm_nusselt_static(int lattice, int nx, int ny, int nz, const int face_kind[6],
                                   const double T_wall[6], double T_ref, const void* g, int face,
@@ -187,17 +225,18 @@ extern "C" int lbm_nusselt_static(int lattice, int nx, int ny, int nz, const int
     const int dim = lat == LBM_D2Q9_D2Q9 ? 2 : 3;
     if (dim == 2 && nz == 0) nz = 1;
     if (nx < 1 || ny < 1 || nz < 1 || (dim == 2 && nz != 1) || (long long)nx * ny * nz > INT_MAX)
-        return err(LBM_EINVAL, "bad box dimensions");
+        return err(LBM_EINVAL, "bad box dimensions %d x %d x %d", nx, ny, nz);
     if (!face_kind || !T_wall || !g || !result) return err(LBM_EINVAL, "NULL argument");
     if (face < 0 || face >= 2 * dim || face_kind[face] != LBM_WALL_FIXED_T)
-        return err(LBM_EINVAL, "face is not a fixed-temperature wall of this box");
+        return err(LBM_EINVAL, "face %d is not a fixed-temperature wall of this box", face);
     if (!(L > 0) || !(dT > 0)) return err(LBM_EINVAL, "L and dT must be positive");
     const int ext[3] = {nx, ny, nz};
     if (ext[face / 2] < 2) return err(LBM_EINVAL, "fewer than two node layers normal to the face");
     const long long n_face = face / 2 == 0 ? (long long)ny * nz
                            : (face / 2 == 1 ? (long long)nx * nz : (long long)nx * ny);
     if (n_face > LBM_NUSSELT_STATIC_MAX_FACE_NODES)
-        return err(LBM_EINVAL, "face has more nodes than LBM_NUSSELT_STATIC_MAX_FACE_NODES");
+        return err(LBM_EINVAL, "face %d has %lld nodes, more than LBM_NUSSELT_STATIC_MAX_FACE_NODES (%d), "
+                   "the room of the fixed scratch array", face, n_face, (int)LBM_NUSSELT_STATIC_MAX_FACE_NODES);
 
     Geometry geo{};
     geo.nx = nx; geo.ny = ny; geo.nz = nz; geo.nxy = nx * ny; geo.n = nx * ny * nz;
@@ -212,12 +251,12 @@ extern "C" int lbm_nusselt_static(int lattice, int nx, int ny, int nz, const int
             return err(LBM_EINVAL, "axis periodic on one face only");
 
     double* scratch = nullptr;
-    cudaError_t e = scratch_address(&scratch);
-    if (e != cudaSuccess) return err(LBM_ECUDA, cudaGetErrorString(e));
+    const int rc = scratch_address(&scratch);
+    if (rc != LBM_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the ticket must start at zero (a call interrupted earlier could have left it otherwise)
-    e = cudaMemsetAsync(scratch + 5 * kMaxBlocks, 0, sizeof(double), st);
-    if (e != cudaSuccess) return err(LBM_ECUDA, cudaGetErrorString(e));
+    cudaError_t e = cudaMemsetAsync(scratch + 5 * kMaxBlocks, 0, sizeof(double), st);
+    if (e != cudaSuccess) return err(LBM_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     const double s = T_wall[face] >= T_ref ? 1.0 : -1.0;
     const double scale = -s * L / dT;
     const int blocks = (int)((n_face + kThreads - 1) / kThreads);
@@ -235,6 +274,7 @@ extern "C" int lbm_nusselt_static(int lattice, int nx, int ny, int nz, const int
     }
 #undef LBM_STATIC_LAUNCH
     e = cudaGetLastError();
-    if (e != cudaSuccess) return err(LBM_ECUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) return err(LBM_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
     return LBM_OK;
 }
+#undef err

@@ -245,11 +245,7 @@ def lbm_nusselt_static(lattice: int, nx: int, ny: int, nz: int, face_kind, T_wal
     st = lib().lbm_nusselt_static(lattice, nx, ny, nz, fk, tw, T_ref, ctypes.c_void_p(g_ptr), face,
                                   L, dT, ctypes.c_void_p(result_ptr), ctypes.c_void_p(stream))
     if st != LBM_OK:
-        ax = face // 2 if 0 <= face < 6 else 0
-        n_face = [ny * nz, nx * nz, nx * ny][ax]
-        why = (f"face {face} has {n_face} nodes, more than {NUSSELT_STATIC_MAX_FACE_NODES}"
-               if n_face > NUSSELT_STATIC_MAX_FACE_NODES else "invalid arguments or CUDA failure")
-        raise LbmError(st, f"lbm_nusselt_static: {why}")
+        raise LbmError(st, lib().lbm_last_error(None).decode() or lib().lbm_status_string(st).decode())
 
 
 def _bcheck(status: int, b=None):
@@ -522,7 +518,7 @@ class Lattice:
 
 
 class Batch:
-    """Many 2D boxes advanced together by one persistent launch per step (lbm_batch_*)."""
+    """Many 2D boxes advanced together by one kernel launch per step (lbm_batch_*)."""
 
     def __init__(self, sizes, Ra, Pr, Ma: float = 0.1, walls=None, precision: str = "fp32",
                  stream=None, torch_allocator: bool = True):

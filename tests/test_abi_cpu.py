@@ -136,3 +136,19 @@ def test_bounded_wait_probe_validates_its_limit(lbm):
         assert lbm.lib().lbm_probe_bounded_wait(bad, ctypes.byref(t)) == lbm.LBM_EINVAL
     assert lbm.lib().lbm_probe_bounded_wait(0.01, None) == lbm.LBM_EINVAL
     assert lbm.lbm_status_string(lbm.LBM_ETIMEOUT) == "a bounded device wait timed out"
+
+
+@pytest.mark.parametrize("n,face,msg", [
+    (1025, 0, "face 0 has 1050625 nodes, more than LBM_NUSSELT_STATIC_MAX_FACE_NODES"),
+    (8, 2, "face 2 is not a fixed-temperature wall"),
+])
+def test_nusselt_static_reports_why_it_rejects_a_call(lbm, n, face, msg):
+    """The allocation-free Nusselt entry validates its arguments before any CUDA call, and
+    lbm_last_error(NULL) on the calling thread carries the library's own reason."""
+    walls = lbm.Walls.cavity(3)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_nusselt_static(lbm.LBM_D3Q27_D3Q15 | lbm.LBM_FP64, 4, n, n, walls.face, walls.T_wall,
+                               walls.T_ref, 16, face, 4.0, 1.0, 16)
+    assert e.value.status == lbm.LBM_EINVAL
+    assert msg in lbm.lbm_last_error(None)
+    assert msg in str(e.value)

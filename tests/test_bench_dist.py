@@ -5,6 +5,7 @@ the max-reduction of their timed windows.  These tests run that host logic with 
 and world size 2, and check the reference arm's rank handling.
 """
 import argparse
+import json
 import os
 import socket
 
@@ -83,3 +84,36 @@ def test_fp64_roofline_uses_the_counted_operations():
     assert r["bound"] == "alu"
     assert r["achieved"] == pytest.approx(500.0 * bench.FP64_OPS_PER_NODE["d3q27"] / 1e3, rel=1e-3)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], rel=1e-3)
+
+
+def test_fp64_roofline_takes_the_device_and_the_sampled_clock():
+    r = bench.fp64_alu_roofline(500.0, "d2q9", sms=148, clock_ghz=1.9, clock_kind="sampled")
+    assert r["peak"] == pytest.approx(148 * bench.FP64_LANE_OPS_PER_SM_CLK * 1.9, rel=1e-3)
+    assert "148 SMs" in r["peak_kind"] and "1.900 GHz" in r["peak_kind"]
+
+
+def test_compact_records_close_the_bench_line():
+    """Every form's figures sit at the end of the JSON line, in a short table."""
+    line = {"value": 17500.0, "dtype": "f32", "roofline": {"achieved": 5900.0, "frac": 0.87, "bound": "hbm"},
+            "config": {"nx": 256, "ny": 256, "nz": 256}}
+    forms = [{"lattice": "D3Q27+D3Q15", "precision": "fp64", "box": [256, 256, 256], "mlups": 560.0,
+              "gbs": 376.3, "hbm_frac": 0.055, "g_attractors": "option A", "l2_resident": False,
+              "roofline": {"frac": 0.87}},
+             {"lattice": "D2Q9+D2Q9", "precision": "fp32", "box": [1024, 512, 1], "mlups": 49000.0,
+              "gbs": 7056.0, "hbm_frac": 1.04, "g_attractors": "option A", "l2_resident": True}]
+    nu = [{"case": "2D cavity 64x64, Ra 1e4, Pr 0.71, 20000 steps",
+           "nu_hot_mean": {"fp64": 2.24, "fp32": 2.2401, "fp16s": 2.242},
+           "rel_vs_fp64": {"fp32": 7.1e-5, "fp16s": 1.1e-3}}]
+    batched = {"nodes": 6303744, "mlups": 43500.0, "gbs": 6264.0, "hbm_frac": 0.92, "speedup_vs_unbatched": 1.6}
+    adjoint = {"adjoint_ms_per_step": 0.03, "forward_ms_per_step": 0.003, "adjoint_over_forward": 10.0}
+    out = bench.append_secondary(dict(line), forms, nu, batched, adjoint, {"value": 4.2})
+    keys = list(out)
+    assert keys[-2:] == ["nu_accuracy", "per_form"]
+    pf = out["per_form"]
+    assert [p["form"] for p in pf] == ["3D f32 (headline)", "3D fp64", "2D fp32",
+                                       "2D fp32 batched ensemble", "2D adjoint 256x256 (double-float VJP)"]
+    assert pf[1]["alu_frac"] == 0.87 and pf[1]["bound"] == "fp64 alu"
+    assert "L2" in pf[2]["note"]
+    assert out["nu_accuracy"][0] == {"case": "2D cavity 64x64, Ra 1e4", "nu_fp64": 2.24,
+                                     "fp32_rel": 7.1e-5, "fp16s_rel": 1.1e-3}
+    assert len(json.dumps({k: out[k] for k in keys[-2:]})) < 2500

@@ -191,6 +191,71 @@ def test_adjoint_256_2000_steps_matches_central_differences(precision, arith, wo
             assert abs(grad @ v - fd) <= 1e-4 * gn * np.linalg.norm(v)
 
 
+@pytest.fixture(scope="module")
+def workload_fd_full():
+    """All 256 central differences dJ/dT_w(j) of the 256^2 adjoint workload, from the FP64 forward
+    on the GPU, at h = 1e-2 and at the configured h = 1e-4 (one handle, its state reset before every
+    run)."""
+    nx = ny = 256
+    steps, Ra = 2000, 1e5
+    prof = synth.sine_profile(2024, ny)
+    lat = L.Lattice("d2q9", nx, ny, Ra=Ra, walls=L.Walls.cavity(2), precision="fp64")
+    state0 = lat.get_state()
+
+    def J(p):
+        lat.set_state(state0)
+        lat.set_wall_profile(HOT, p)
+        lat.step(steps)
+        return lat.nusselt(COLD)[0]
+
+    J0 = J(prof)
+    assert J(prof) == J0                     # the forward is deterministic
+    fd = {}
+    for h in (1e-2, 1e-4):
+        d = np.zeros(ny)
+        for j in range(ny):
+            e = np.zeros(ny)
+            e[j] = h
+            d[j] = (J(prof + e) - J(prof - e)) / (2 * h)
+        fd[h] = d
+    lat.close()
+    return prof, fd
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_adjoint_256_whole_gradient_matches_central_differences(precision, workload_fd_full):
+    """The whole design gradient of the adjoint workload (256^2, Ra 1e5, 2000 steps, default
+    double-float VJPs with FP64 accumulation) against all 256 central differences of the FP64
+    forward: ||g - g_FD|| / ||g_FD|| <= 1e-4, at h = 1e-2 and at h = 1e-4.
+    Noise of the differences: J (~6.85) carries a few 1e-15 of rounding from 2000 steps, which over
+    2h is 3e-11 per component at h = 1e-4 (components are ~4e-7, so 1e-4 of each) and 3e-13 at
+    h = 1e-2; the truncation error of h = 1e-2 (h^2 / 6 times the third derivative) stays below 1e-8
+    of the gradient, as on the small cavity.  Per component, every difference at h = 1e-2 larger
+    than 1e-3 of the largest (all but the few near sign changes, far above the 3e-13 floor) is
+    matched within 1e-4 of itself (FP64 states) or within 1e-4 of the largest (FP32 states, which
+    the adjoint linearises about; their rounding moves small components by a few 1e-4 of
+    themselves)."""
+    prof, fd = workload_fd_full
+    lat = L.Lattice("d2q9", 256, 256, Ra=1e5, walls=L.Walls.cavity(2), precision=precision)
+    lat.set_wall_profile(HOT, prof)
+    _, g = lat.adjoint(2000, COLD, HOT)
+    lat.close()
+    for h, d in fd.items():
+        rel = np.linalg.norm(g - d) / np.linalg.norm(d)
+        print(f"{precision} h={h:g}: ||g - fd|| / ||fd|| = {rel:.3e}")
+        assert rel <= 1e-4, (h, rel)
+    d = fd[1e-2]
+    big = np.abs(d) > 1e-3 * np.abs(d).max()
+    assert big.sum() >= 200
+    err = np.abs(g - d)[big]
+    worst = (err / np.abs(d[big])).max()
+    print(f"{precision}: per-component worst |g - fd| / |fd| = {worst:.3e} over {big.sum()} components")
+    if precision == "fp64":
+        assert worst <= 1e-4
+    else:
+        assert err.max() <= 1e-4 * np.abs(d).max()
+
+
 def test_torch_autograd_function_returns_the_adjoint_gradient():
     nx, ny, steps = 28, 24, 60
     lat = L.Lattice("d2q9", nx, ny, Ra=1e5, walls=L.Walls.cavity(2), precision="fp64")
