@@ -138,6 +138,10 @@ LBM_API int lbm_set_omegas(lbm_handle h, const double* om_f, int n_f, const doub
  * stochastically, up or down with probabilities that make the rounding unbiased, so that updates
  * smaller than half an FP16 step accumulate in expectation; 0 rounds to nearest), "adjoint_arith" (arithmetic of lbm_adjoint_step's vector-Jacobian products and adjoint state: 2, the default, double-float, i.e. pairs of FP32
  * numbers with a 48-bit significand evaluated on the FP32 pipes; 1 FP64; 0 FP32), "adjoint_fp64" (0 or 1: the same as "adjoint_arith" 0 or 1),
+ * "adjoint_sync" (thread blocks of the adjoint kernel: 0 = 64 x 2; 1-4 = 64 x 4, 128 x 2 (the
+ * default), 32 x 4, 64 x 2 whose warps pass a barrier between the phases of the node's work so
+ * that they share the instruction fetches of the long unrolled product; results agree to
+ * rounding),
  * "graph_steps" (even count of steps that lbm_step replays as one CUDA graph; 0 disables),
  * "index64" (1: the step kernels use 64-bit element offsets, the instantiation that boxes with
  * q n >= 2^32 run, on any box; results are bitwise those of the 32-bit form; for testing that path), or the
@@ -202,9 +206,10 @@ LBM_API int lbm_set_wall_profile(lbm_handle h, int face, const double* T_w, long
  * K = ceil(sqrt(n_steps)) steps, then n_steps fused adjoint steps backward, recomputing each
  * segment of K states once from its checkpoint: about 2 sqrt(n_steps) states of device memory and
  * one extra forward pass.  The vector-Jacobian products of the collision are evaluated at the
- * stored states in double-float arithmetic by default: the gradient equals the FP64 adjoint's to
- * about 1e-12 relative, at a third of its cost on GPUs whose FP64 rate is a small fraction of
- * their FP32 rate.  lbm_set_param "adjoint_arith" = 1 selects FP64, 0 FP32 (about twice as fast
+ * recomputed forward intermediates of each node (in the forward step's own register type, FP32
+ * for FP32 / FP16 states), with the adjoint carried in double-float arithmetic by default: the
+ * gradient equals the FP64 adjoint's to about 1e-11 relative, at a third of its cost on GPUs whose
+ * FP64 rate is a small fraction of their FP32 rate.  lbm_set_param "adjoint_arith" = 1 selects FP64, 0 FP32 (about twice as fast
  * again, gradients to about 1e-4 relative after 2000 steps).  The design gradient is always
  * accumulated in FP64.  2D (D2Q9 pair) only.
  * J and grad_Tw are host pointers; n must equal the number of design-face nodes.

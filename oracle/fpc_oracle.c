@@ -797,14 +797,22 @@ void orc_get_state(const orc_grid *G, double *f, double *g)
 
 /*
  * Source node of the link arriving at (x, y, z) along e, after wrapping periodic axes.
- * Returns -1 if the source lies beyond a wall; then *fixed is the first crossed fixed-T face
- * (or -1 if every crossed face is adiabatic).
+ * Returns -1 if the source lies beyond a wall.  A link across an edge or corner of the box
+ * crosses two or three walls; the one that decides its rule is the crossed face that comes last
+ * in the order -z, -y, -x, +x, +y, +z (reading R7).  *fixed is that face when it has a fixed
+ * temperature (anti-bounce-back), else -1 (bounce-back).
  */
+static int face_rank(int face)
+{
+    static const int rank[6] = {2, 3, 1, 4, 0, 5};   /* -x, +x, -y, +y, -z, +z */
+    return rank[face];
+}
+
 static long link_source(const orc_grid *G, int x, int y, int z, const int e[3], int *fixed)
 {
     int s[3] = {x - e[0], y - e[1], z - e[2]};
     const int ext[3] = {G->nx, G->ny, G->nz};
-    int outside = 0;
+    int decide = -1;
     *fixed = -1;
     for (int ax = 0; ax < G->dim; ++ax) {
         int face = -1;
@@ -815,10 +823,12 @@ static long link_source(const orc_grid *G, int x, int y, int z, const int e[3], 
             s[ax] = (s[ax] + ext[ax]) % ext[ax];
             continue;
         }
-        outside = 1;
-        if (G->face_bc[face] == ORC_WALL_FIXED_T && *fixed < 0) *fixed = face;
+        if (decide < 0 || face_rank(face) > face_rank(decide)) decide = face;
     }
-    if (outside) return -1;
+    if (decide >= 0) {
+        if (G->face_bc[decide] == ORC_WALL_FIXED_T) *fixed = decide;
+        return -1;
+    }
     return s[0] + (long)G->nx * (s[1] + (long)G->ny * s[2]);
 }
 

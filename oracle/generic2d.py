@@ -12,8 +12,9 @@ rather than from its printed step-by-step formulas (which fpc_oracle.c follows):
     readings R5, R8, R9) and App. B Step 3 (energy, option A, Eq. MvT2D, or option B,
     Eq. MvT2DoptionB), on those moments;
   * the pull streaming of Eqs. LBMsteps-stream / LBMsteps-streamg with the half-way walls of
-    Sec. 6.1 (bounce-back of f, bounce-back or anti-bounce-back of g at the first fixed-T face
-    crossed, reading R7), the Boussinesq force and velocity of App. A Step 7 (reading R10), and the
+    Sec. 6.1 (bounce-back of f; bounce-back or anti-bounce-back of g, decided at edge links by the
+    crossed face that comes last in the order -y, -x, +x, +y, reading R7), the Boussinesq force and
+    velocity of App. A Step 7 (reading R10), and the
     wall Nusselt number of Sec. 6.1 (readings R13-R15).
 
 Every node is processed at once with numpy arrays of shape (9, ny, nx).  With dtype complex128
@@ -32,6 +33,8 @@ W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)    # rest-state attractor wei
 MOMENTS = [(0, 0), (1, 0), (0, 1), (2, 0), (0, 2), (1, 1), (2, 1), (1, 2), (2, 2)]
 CS2 = 1.0 / 3.0
 PERIODIC, WALL_ADIABATIC, WALL_FIXED_T = 0, 1, 2
+# faces -x, +x, -y, +y in the order that decides edge links (reading R7): -y, -x, +x, +y
+FACE_RANK = {0: 1, 1: 2, 2: 0, 3: 3}
 
 
 def central_matrix(ux, uy):
@@ -136,14 +139,18 @@ class Generic2D:
             sx, sy = x - E[a, 0], y - E[a, 1]
             out = np.zeros((ny, nx), dtype=bool)
             fixed = -np.ones((ny, nx), dtype=np.int64)
+            rank = -np.ones((ny, nx), dtype=np.int64)       # rank of the deciding face so far
             for ax, (c, ext) in enumerate(((sx, nx), (sy, ny))):
                 for face, beyond in ((2 * ax, c < 0), (2 * ax + 1, c >= ext)):
                     if self.face[face] == PERIODIC:
                         c[beyond] = (c[beyond] + ext) % ext
                     else:
                         out |= beyond
-                        if self.face[face] == WALL_FIXED_T:
-                            fixed[(fixed < 0) & beyond] = face
+                        # an edge link takes the rule of the crossed face that comes last in the
+                        # order -y, -x, +x, +y (reading R7)
+                        wins = beyond & (FACE_RANK[face] > rank)
+                        rank[wins] = FACE_RANK[face]
+                        fixed[wins] = face if self.face[face] == WALL_FIXED_T else -1
             self.src[a] = np.where(out, 0, sx + nx * sy)
             self.out[a] = out
             self.fixed[a] = fixed

@@ -26,18 +26,20 @@ static cudaError_t run_adjoint(const void* f_prev, const void* g_prev, const voi
     using T = typename S::T;
     using R = typename S::R;
     if (hc.adj_sync) {
-        const dim3 b(hc.adj_sync == 2 ? 128 : 64, hc.adj_sync == 2 ? 2 : 4, 1);
+        // thread blocks of the barrier-phased kernel: 64x4, 128x2, 32x4 or 64x2
+        const int shapes[5][2] = {{0, 0}, {64, 4}, {128, 2}, {32, 4}, {64, 2}};
+        const dim3 b(shapes[hc.adj_sync][0], shapes[hc.adj_sync][1], 1);
         const dim3 grid((geo.nx + b.x - 1) / b.x, (geo.ny + b.y - 1) / b.y, 1);
         adjoint_step_d2q9_kernel<S, RT, true><<<grid, b, 0, st>>>(
             (const T*)f_prev, (const T*)g_prev, (const RT*)mu_in, (RT*)mu_out, geo,
-            make_coeffs<R, 9, 9>(hc), make_coeffs<RT, 9, 9>(hc), design_face, grad);
+            make_coeffs<R, 9, 9>(hc), make_coeffs<TapeT<R, RT>, 9, 9>(hc), design_face, grad);
         return cudaGetLastError();
     }
     const dim3 b(64, 2, 1);
     const dim3 grid((geo.nx + b.x - 1) / b.x, (geo.ny + b.y - 1) / b.y, 1);
     adjoint_step_d2q9_kernel<S, RT><<<grid, b, 0, st>>>(
         (const T*)f_prev, (const T*)g_prev, (const RT*)mu_in, (RT*)mu_out, geo,
-        make_coeffs<R, 9, 9>(hc), make_coeffs<RT, 9, 9>(hc), design_face, grad);
+        make_coeffs<R, 9, 9>(hc), make_coeffs<TapeT<R, RT>, 9, 9>(hc), design_face, grad);
     return cudaGetLastError();
 }
 

@@ -16,47 +16,85 @@
 // arithmetic operators and instantiated for each.
 #pragma once
 
+#include <type_traits>
+
 #include "dfloat.cuh"
 #include "step_d2q9.cuh"
 
 namespace lbm {
 
+// Reverse-mode products multiply an adjoint value (type RT) by a forward value of the node's
+// collision (type RF).  The forward values are the forward step's own intermediates: for FP32 /
+// FP16 states they are FP32 numbers (RF = float), computed with the same FP32 arithmetic as the
+// forward step, and the products, which carry the adjoint, are formed in RT; for FP64 states
+// RF = RT.  Quantities that depend on forward values only (the Jacobian's entries) are evaluated
+// in RF.
+template <class R, class RT>
+using TapeT = typename std::conditional<std::is_same<R, float>::value, float, RT>::type;
+
+// adjoint times forward value
+template <class RT, class RF>
+__device__ __forceinline__ auto am(RT a, RF f)
+{
+    return a * RT(f);
+}
+// A double-float adjoint times an FP32 forward value: the leading product with its exact error
+// plus the low part's product, left unnormalized for the sum that consumes it (3 flops instead of
+// the 4 of a double-float product).
+__device__ __forceinline__ dfprod am(dfloat a, float f)
+{
+    const float p = __fmul_rn(a.hi, f);
+    float e = __fmaf_rn(a.hi, f, -p);
+    e = __fmaf_rn(a.lo, f, e);
+    return dfprod{p, e};
+}
+__device__ __forceinline__ dfprod am(dfprod a, float f) { return am(dfloat(a), f); }
+
+// x / 2 (exact)
+template <class RT>
+__device__ __forceinline__ RT halve(RT x)
+{
+    return x * RT(0.5);
+}
+__device__ __forceinline__ dfloat halve(dfloat x) { return dfloat(__fmul_rn(0.5f, x.hi), __fmul_rn(0.5f, x.lo)); }
+
 // Reverse of central_line: outputs (k0, k1, k2) of the line at velocity u with adjoints
 // (K0, K1, K2); returns the adjoints (Ab, Bb, Cb) of the inputs and adds d(...)/du to ubar.
-template <class RT>
-__device__ __forceinline__ void central_line_vjp(RT k0, RT k1, RT u, RT K0, RT K1, RT K2, RT& Ab,
+template <class RT, class RF>
+__device__ __forceinline__ void central_line_vjp(RF k0, RF k1, RF u, RT K0, RT K1, RT K2, RT& Ab,
                                                  RT& Bb, RT& Cb, RT& ubar)
 {
-    const RT d = k1 + u * k0;          // c - a
-    const RT K1t = K1 - u * K2;        // total adjoint of k1
-    const RT Sb = K2;                  // adjoint of s = c + a
-    const RT Db = K1t - u * K2;        // adjoint of d
-    const RT K0t = K0 - u * K1t;       // total adjoint of k0
-    ubar += -K2 * (d + k1) - K1t * k0;
-    Ab = K0t - Db + Sb;
+    const RF d = k1 + u * k0;          // c - a
+    const auto uK2 = am(K2, u);
+    const RT K1t = K1 - uK2;           // total adjoint of k1
+    const RT Db = K1t - uK2;           // adjoint of d; K2 is the adjoint of s = c + a
+    const RT K0t = K0 - am(K1t, u);    // total adjoint of k0
+    ubar -= am(K2, d + k1) + am(K1t, k0);
+    Ab = (K0t - Db) + K2;
     Bb = K0t;
-    Cb = K0t + Db + Sb;
+    Cb = (K0t + Db) + K2;
 }
 
 // Reverse of uncentral_line: inputs (k0, k1, k2) at velocity u, adjoints (Ab, Bb, Cb) of the
 // three links; returns the adjoints of (k0, k1, k2) and adds d(...)/du to ubar.
-template <class RT>
-__device__ __forceinline__ void uncentral_line_vjp(RT k0, RT k1, RT u, RT Ab, RT Bb, RT Cb, RT& K0,
+template <class RT, class RF>
+__device__ __forceinline__ void uncentral_line_vjp(RF k0, RF k1, RF u, RT Ab, RT Bb, RT Cb, RT& K0,
                                                    RT& K1, RT& K2, RT& ubar)
 {
-    const RT h = RT(0.5);
-    const RT r1 = k1 + u * k0;
-    const RT R2 = h * Ab - Bb + h * Cb;
-    const RT R1 = -h * Ab + h * Cb + u * R2;
+    const RF r1 = k1 + u * k0;
+    const RT hA = halve(Ab), hC = halve(Cb);
+    const RT R2 = (hA - Bb) + hC;
+    const auto uR2 = am(R2, u);
+    const RT R1 = (hC - hA) + uR2;
     K2 = R2;
-    K1 = u * R2 + R1;
-    K0 = Bb + u * R1;
-    ubar += R2 * (k1 + r1) + R1 * k0;
+    K1 = R1 + uR2;
+    K0 = Bb + am(R1, u);
+    ubar += am(R2, k1 + r1) + am(R1, k0);
 }
 
 // Forward sweeps keeping the intermediate values the reverse needs.
-template <class RT>
-__device__ __forceinline__ void sweeps_fwd(const RT in[9], RT X[3][3], RT D[3][3], RT ux, RT uy)
+template <class R>
+__device__ __forceinline__ void sweeps_fwd(const R in[9], R X[3][3], R D[3][3], R ux, R uy)
 {
     static_for<9>([&](auto I) {
         constexpr int a = decltype(I)::value;
@@ -73,9 +111,9 @@ __device__ __forceinline__ void sweeps_fwd(const RT in[9], RT X[3][3], RT D[3][3
 }
 
 // Reverse of sweeps_fwd: adjoints Db of D -> adjoints of the 9 inputs, ux/uy adjoints.
-template <class RT>
-__device__ __forceinline__ void sweeps_vjp(const RT X[3][3], const RT D[3][3], const RT Db[3][3],
-                                           RT ux, RT uy, RT inb[9], RT& uxb, RT& uyb)
+template <class RT, class RF>
+__device__ __forceinline__ void sweeps_vjp(const RF X[3][3], const RF D[3][3], const RT Db[3][3],
+                                           RF ux, RF uy, RT inb[9], RT& uxb, RT& uyb)
 {
     RT Xb[3][3];
 #pragma unroll
@@ -94,8 +132,8 @@ __device__ __forceinline__ void sweeps_vjp(const RT X[3][3], const RT D[3][3], c
 }
 
 // Forward inverse sweeps keeping the values the reverse needs: T (relaxed moments) -> Y.
-template <class RT>
-__device__ __forceinline__ void unsweeps_fwd(const RT T[3][3], RT Y[3][3], RT uy)
+template <class R>
+__device__ __forceinline__ void unsweeps_fwd(const R T[3][3], R Y[3][3], R uy)
 {
 #pragma unroll
     for (int j = 0; j < 3; ++j)
@@ -106,9 +144,9 @@ __device__ __forceinline__ void unsweeps_fwd(const RT T[3][3], RT Y[3][3], RT uy
 }
 
 // Reverse of the inverse sweeps: adjoints of the 9 outputs -> adjoints Tb of T.
-template <class RT>
-__device__ __forceinline__ void unsweeps_vjp(const RT T[3][3], const RT Y[3][3], const RT outb[9],
-                                             RT ux, RT uy, RT Tb[3][3], RT& uxb, RT& uyb)
+template <class RT, class RF>
+__device__ __forceinline__ void unsweeps_vjp(const RF T[3][3], const RF Y[3][3], const RT outb[9],
+                                             RF ux, RF uy, RT Tb[3][3], RT& uxb, RT& uyb)
 {
     RT Ob[3][3];
     static_for<9>([&](auto I) {
@@ -128,112 +166,109 @@ __device__ __forceinline__ void unsweeps_vjp(const RT T[3][3], const RT Y[3][3],
 
 // Reverse of relax_f_d2q9 (deviation form): adjoints tb of the relaxed deviations T -> adjoints
 // Db of the pre-collision deviations D and of drho, irho, ux, uy, Fx, Fy.
-template <class RT>
-__device__ __forceinline__ void relax_f_d2q9_vjp(const RT D[3][3], RT drho, RT irho, RT ux, RT uy,
-                                                 RT Fx, RT Fy, const Coeffs2D<RT>& c,
+template <class RT, class RF>
+__device__ __forceinline__ void relax_f_d2q9_vjp(const RF D[3][3], RF drho, RF irho, RF ux, RF uy,
+                                                 RF Fx, RF Fy, const Coeffs2D<RF>& c,
                                                  const RT tb[3][3], RT Db[3][3], RT& drhob,
                                                  RT& irhob, RT& uxb, RT& uyb, RT& Fxb, RT& Fyb)
 {
-    const RT* o = c.om_f;
-    const RT* h = c.hf;
-    const RT one = RT(1), two = RT(2), half = RT(0.5), two3 = RT(2.0 / 3.0);
-    const RT third = RT(1.0 / 3.0);
-    const RT Ax = third + ux * ux, By = third + uy * uy, uxuy = ux * uy;
-    const RT D20 = D[0][2], D01 = D[1][0], D11 = D[1][1], D21 = D[1][2];
-    const RT D02 = D[2][0], D12 = D[2][1];
-    const RT Fxr = Fx * irho, Fyr = Fy * irho;
-    const RT k11 = uxuy + D11, k20 = Ax + D20, k02 = By + D02;
-    const RT k21 = D21 - Ax * uy, k12 = D12 - ux * By;
-    (void)D01;
-    // forward values needed by the reverse
-    const RT D2s = D20 + D02, D2d = D20 - D02;
-    const RT u2s = ux * ux + uy * uy, u2d = ux * ux - uy * uy;
-    const RT T2s = D2s + o[3] * (two3 * drho - u2s - D2s);
-    const RT T2d = D2d - o[4] * (D2d + u2d);
-    const RT T11 = D11 - o[5] * (D11 + uxuy);
-    const RT T20 = half * (T2s + T2d), T02 = half * (T2s - T2d);
-    const RT t11 = uxuy + T11;
-    const RT N = Ax * T02 + By * T20 + T20 * T02 + two * t11 * t11 - Ax * By * drho;
+    const RF* o = c.om_f;
+    const RF* h = c.hf;
+    const RF one = RF(1), two = RF(2), half = RF(0.5), two3 = RF(2.0 / 3.0);
+    const RF third = RF(1.0 / 3.0);
+    // forward values (the Jacobian's entries depend on these only)
+    const RF Ax = third + ux * ux, By = third + uy * uy, uxuy = ux * uy;
+    const RF D20 = D[0][2], D11 = D[1][1], D21 = D[1][2];
+    const RF D02 = D[2][0], D12 = D[2][1];
+    const RF Fxr = Fx * irho, Fyr = Fy * irho;
+    const RF k11 = uxuy + D11, k20 = Ax + D20, k02 = By + D02;
+    const RF k21 = D21 - Ax * uy, k12 = D12 - ux * By;
+    const RF D2s = D20 + D02, D2d = D20 - D02;
+    const RF u2s = ux * ux + uy * uy, u2d = ux * ux - uy * uy;
+    const RF T2s = D2s + o[3] * (two3 * drho - u2s - D2s);
+    const RF T2d = D2d - o[4] * (D2d + u2d);
+    const RF T11 = D11 - o[5] * (D11 + uxuy);
+    const RF T20 = half * (T2s + T2d), T02 = half * (T2s - T2d);
+    const RF t11 = uxuy + T11;
+    const RF N = Ax * T02 + By * T20 + T20 * T02 + two * t11 * t11 - Ax * By * drho;
 
     const RT a00 = tb[0][0], a10 = tb[0][1], a20 = tb[0][2];
     const RT a01 = tb[1][0], a11 = tb[1][1], a21 = tb[1][2];
     const RT a02 = tb[2][0], a12 = tb[2][1], a22 = tb[2][2];
-    RT d00 = 0, d10 = 0, d20 = 0, d01 = 0, d11 = 0, d21 = 0, d02 = 0, d12 = 0, d22 = 0;
-    RT Axb = 0, Byb = 0, uxuyb = 0, s21b = 0, s12b = 0, s22b = 0;
 
     // T22 = D22 + o8 (M22 - D22) + h8 s22, M22 = N irho
-    d22 += a22 * (one - o[8]);
-    const RT M22b = a22 * o[8];
-    s22b += a22 * h[8];
-    const RT Nb = M22b * irho;
-    irhob += M22b * N;
-    Axb += Nb * (T02 - By * drho);
-    Byb += Nb * (T20 - Ax * drho);
-    const RT T02b = a02 + Nb * (Ax + T20);
-    const RT T20b = a20 + Nb * (By + T02);
-    const RT t11b = Nb * RT(4) * t11;
-    drhob += -Nb * Ax * By;
-    uxuyb += t11b;
+    const RT d22 = am(a22, one - o[8]);
+    const RT M22b = am(a22, o[8]);
+    const RT s22b = am(a22, h[8]);
+    const RT Nb = am(M22b, irho);
+    irhob += am(M22b, N);
+    RT Axb = am(Nb, T02 - By * drho);
+    RT Byb = am(Nb, T20 - Ax * drho);
+    const RT T02b = a02 + am(Nb, Ax + T20);
+    const RT T20b = a20 + am(Nb, By + T02);
+    const RT t11b = am(Nb, RF(4) * t11);
+    drhob -= am(Nb, Ax * By);
+    RT uxuyb = t11b;
     const RT T11b = a11 + t11b;
     // T12 = D12 - o7 (D12 - ux B) + h7 s12
-    d12 += a12 * (one - o[7]);
-    uxb += a12 * o[7] * By;
-    Byb += a12 * o[7] * ux;
-    s12b += a12 * h[7];
+    RT d12 = am(a12, one - o[7]);
+    uxb += am(a12, o[7] * By);
+    Byb += am(a12, o[7] * ux);
+    const RT s12b = am(a12, h[7]);
     // T21 = D21 - o6 (D21 - A uy) + h6 s21
-    d21 += a21 * (one - o[6]);
-    Axb += a21 * o[6] * uy;
-    uyb += a21 * o[6] * Ax;
-    s21b += a21 * h[6];
+    RT d21 = am(a21, one - o[6]);
+    Axb += am(a21, o[6] * uy);
+    uyb += am(a21, o[6] * Ax);
+    const RT s21b = am(a21, h[6]);
     // T20, T02 from T2s, T2d
-    const RT T2sb = half * (T20b + T02b), T2db = half * (T20b - T02b);
+    const RT T2sb = halve(T20b + T02b), T2db = halve(T20b - T02b);
     // T11 = D11 - o5 (D11 + uxuy)
-    d11 += T11b * (one - o[5]);
-    uxuyb += -T11b * o[5];
+    RT d11 = am(T11b, one - o[5]);
+    uxuyb -= am(T11b, o[5]);
     // T2d = D2d - o4 (D2d + u2d); T2s = D2s + o3 (2/3 drho - u2s - D2s)
-    const RT D2db = T2db * (one - o[4]);
-    const RT u2db = -T2db * o[4];
-    const RT D2sb = T2sb * (one - o[3]);
-    drhob += T2sb * o[3] * two3;
-    const RT u2sb = -T2sb * o[3];
-    d20 += D2sb + D2db;
-    d02 += D2sb - D2db;
-    uxb += two * ux * (u2sb + u2db);
-    uyb += two * uy * (u2sb - u2db);
+    const RT D2db = am(T2db, one - o[4]);
+    const RT u2db = -am(T2db, o[4]);
+    const RT D2sb = am(T2sb, one - o[3]);
+    drhob += am(T2sb, o[3] * two3);
+    const RT u2sb = -am(T2sb, o[3]);
+    RT d20 = D2sb + D2db;
+    RT d02 = D2sb - D2db;
+    uxb += am(u2sb + u2db, two * ux);
+    uyb += am(u2sb - u2db, two * uy);
     // T01 = D01 - o2 (D01 - uy) + h2 Fy; T10 = D10 - o1 (D10 - ux) + h1 Fx; T00
-    d01 += a01 * (one - o[2]);
-    uyb += a01 * o[2];
-    Fyb += a01 * h[2];
-    d10 += a10 * (one - o[1]);
-    uxb += a10 * o[1];
-    Fxb += a10 * h[1];
-    d00 += a00 * (one - o[0]);
-    drhob += a00 * o[0];
+    const RT d01 = am(a01, one - o[2]);
+    uyb += am(a01, o[2]);
+    Fyb += am(a01, h[2]);
+    const RT d10 = am(a10, one - o[1]);
+    uxb += am(a10, o[1]);
+    Fxb += am(a10, h[1]);
+    const RT d00 = am(a00, one - o[0]);
+    drhob += am(a00, o[0]);
     // sources: s21 = 2 Fxr k11 + Fyr k20; s12 = Fxr k02 + 2 Fyr k11; s22 = 2 (Fxr k12 + Fyr k21)
-    const RT Fxrb = two * s21b * k11 + s12b * k02 + two * s22b * k12;
-    const RT Fyrb = s21b * k20 + two * s12b * k11 + two * s22b * k21;
-    const RT k11b = two * s21b * Fxr + two * s12b * Fyr;
-    const RT k20b = s21b * Fyr;
-    const RT k02b = s12b * Fxr;
-    const RT k12b = two * s22b * Fxr;
-    const RT k21b = two * s22b * Fyr;
+    const RT Fxrb = am(s21b, two * k11) + am(s12b, k02) + am(s22b, two * k12);
+    const RT Fyrb = am(s21b, k20) + am(s12b, two * k11) + am(s22b, two * k21);
+    const RT k11b = am(s21b, two * Fxr) + am(s12b, two * Fyr);
+    const RT k20b = am(s21b, Fyr);
+    const RT k02b = am(s12b, Fxr);
+    const RT k12b = am(s22b, two * Fxr);
+    const RT k21b = am(s22b, two * Fyr);
     d12 += k12b;
-    uxb += -k12b * By;
-    Byb += -k12b * ux;
+    uxb -= am(k12b, By);
+    Byb -= am(k12b, ux);
     d21 += k21b;
-    Axb += -k21b * uy;
-    uyb += -k21b * Ax;
+    Axb -= am(k21b, uy);
+    uyb -= am(k21b, Ax);
     Byb += k02b;
     d02 += k02b;
     Axb += k20b;
     d20 += k20b;
     uxuyb += k11b;
     d11 += k11b;
-    Fxb += Fxrb * irho;
-    Fyb += Fyrb * irho;
-    irhob += Fxrb * Fx + Fyrb * Fy;
-    uxb += uxuyb * uy + two * ux * Axb;
-    uyb += uxuyb * ux + two * uy * Byb;
+    Fxb += am(Fxrb, irho);
+    Fyb += am(Fyrb, irho);
+    irhob += am(Fxrb, Fx) + am(Fyrb, Fy);
+    uxb += am(uxuyb, uy) + am(Axb, two * ux);
+    uyb += am(uxuyb, ux) + am(Byb, two * uy);
 
     Db[0][0] = d00; Db[0][1] = d10; Db[0][2] = d20;
     Db[1][0] = d01; Db[1][1] = d11; Db[1][2] = d21;
@@ -242,52 +277,54 @@ __device__ __forceinline__ void relax_f_d2q9_vjp(const RT D[3][3], RT drho, RT i
 
 // Reverse of relax_g_d2q9 (full values): adjoints tb of eta~ -> adjoints nb of eta and of T.
 // t holds the forward post-collision moments eta~ (needed by the option-B attractors).
-template <class RT>
-__device__ __forceinline__ void relax_g_d2q9_vjp(const Coeffs2D<RT>& c, const RT t[3][3], RT T,
+template <class RT, class RF>
+__device__ __forceinline__ void relax_g_d2q9_vjp(const Coeffs2D<RF>& c, const RF t[3][3], RF T,
                                                  const RT tb[3][3], RT nb[3][3], RT& Tb)
 {
-    const RT* o = c.om_g;
-    const RT one = RT(1), half = RT(0.5), two = RT(2);
-    const RT cs2 = RT(1.0 / 3.0);
+    const RF* o = c.om_g;
+    const RF one = RF(1), two = RF(2);
+    const RF cs2 = RF(1.0 / 3.0);
     const RT a00 = tb[0][0], a10 = tb[0][1], a20 = tb[0][2];
     const RT a01 = tb[1][0], a11 = tb[1][1], a21 = tb[1][2];
     const RT a02 = tb[2][0], a12 = tb[2][1], a22 = tb[2][2];
     // t21, t12, t22 = n + o (Mv - n) with attractors from the post-collision lower moments
-    const RT n21b = a21 * (one - o[6]), M21b = a21 * o[6];
-    const RT n12b = a12 * (one - o[7]), M12b = a12 * o[7];
-    const RT n22b = a22 * (one - o[8]), M22b = a22 * o[8];
+    const RT n21b = am(a21, one - o[6]), M21b = am(a21, o[6]);
+    const RT n12b = am(a12, one - o[7]), M12b = am(a12, o[7]);
+    const RT n22b = am(a22, one - o[8]), M22b = am(a22, o[8]);
     RT t10b = a10, t01b = a01, t20b = a20, t02b = a02, t11b = a11;
     if (c.gopt == 0) {
         // Mv21 = (2/3) c_s^2 t01, Mv12 = (2/3) c_s^2 t10, Mv22 = (1/2) c_s^2 (t20 + t02)
-        const RT c1 = RT(2.0 / 9.0), c2 = RT(1.0 / 6.0);
-        t01b += c1 * M21b;
-        t10b += c1 * M12b;
-        t20b += c2 * M22b;
-        t02b += c2 * M22b;
+        const RF c1 = RF(2.0 / 9.0), c2 = RF(1.0 / 6.0);
+        t01b += am(M21b, c1);
+        t10b += am(M12b, c1);
+        t20b += am(M22b, c2);
+        t02b += am(M22b, c2);
     } else {
         // Mv21 = c23 (t20 t01 + 2 t11 t10), Mv12 = c23 (t02 t10 + 2 t11 t01),
         // Mv22 = (t20 t02 + 2 t11^2) / T, c23 = 2 / (3 T)
-        const RT t10 = t[0][1], t01 = t[1][0], t20 = t[0][2], t02 = t[2][0], t11 = t[1][1];
-        const RT iT = one / T, c23 = RT(2.0 / 3.0) * iT;
-        const RT P21 = t20 * t01 + two * t11 * t10;
-        const RT P12 = t02 * t10 + two * t11 * t01;
-        const RT P22 = t20 * t02 + two * t11 * t11;
-        const RT g21 = M21b * c23, g12 = M12b * c23, g22 = M22b * iT;
-        t20b += g21 * t01 + g22 * t02;
-        t02b += g12 * t10 + g22 * t20;
-        t01b += g21 * t20 + two * g12 * t11;
-        t10b += two * g21 * t11 + g12 * t02;
-        t11b += two * (g21 * t10 + g12 * t01) + RT(4) * g22 * t11;
-        Tb += -(g21 * P21 + g12 * P12 + g22 * P22) * iT;
+        const RF t10 = t[0][1], t01 = t[1][0], t20 = t[0][2], t02 = t[2][0], t11 = t[1][1];
+        const RF iT = one / T, c23 = RF(2.0 / 3.0) * iT;
+        const RF P21 = t20 * t01 + two * t11 * t10;
+        const RF P12 = t02 * t10 + two * t11 * t01;
+        const RF P22 = t20 * t02 + two * t11 * t11;
+        const RT g21 = am(M21b, c23), g12 = am(M12b, c23), g22 = am(M22b, iT);
+        t20b += am(g21, t01) + am(g22, t02);
+        t02b += am(g12, t10) + am(g22, t20);
+        t01b += am(g21, t20) + am(g12, two * t11);
+        t10b += am(g21, two * t11) + am(g12, t02);
+        t11b += am(g21, two * t10) + am(g12, two * t01);
+        t11b += am(g22, RF(4) * t11);
+        const RT Pb = am(g21, P21) + am(g12, P12);
+        Tb -= am(Pb + am(g22, P22), iT);
     }
-    const RT t2sb = half * (t20b + t02b), t2db = half * (t20b - t02b);
-    const RT n2sb = t2sb * (one - o[3]);
-    Tb += t2sb * o[3] * two * cs2 + a00 * o[0];
-    const RT n2db = t2db * (one - o[4]);
-    nb[0][0] = a00 * (one - o[0]);
-    nb[0][1] = t10b * (one - o[1]);
-    nb[1][0] = t01b * (one - o[2]);
-    nb[1][1] = t11b * (one - o[5]);
+    const RT t2sb = halve(t20b + t02b), t2db = halve(t20b - t02b);
+    const RT n2sb = am(t2sb, one - o[3]);
+    Tb += am(t2sb, o[3] * two * cs2) + am(a00, o[0]);
+    const RT n2db = am(t2db, one - o[4]);
+    nb[0][0] = am(a00, one - o[0]);
+    nb[0][1] = am(t10b, one - o[1]);
+    nb[1][0] = am(t01b, one - o[2]);
+    nb[1][1] = am(t11b, one - o[5]);
     nb[0][2] = n2sb + n2db;
     nb[2][0] = n2sb - n2db;
     nb[1][2] = n21b;
@@ -296,46 +333,47 @@ __device__ __forceinline__ void relax_g_d2q9_vjp(const Coeffs2D<RT>& c, const RT
 }
 
 // Forward values of one node's collision that its vector-Jacobian product needs, computed in the
-// register type RF of the forward step (FP32 for FP32 / FP16S states: the same arithmetic the
-// forward step applied) and handed to the reverse in RT.
-template <class RT>
+// register type R of the forward step (FP32 for FP32 / FP16S states: the same arithmetic the
+// forward step applied) and kept in RF (TapeT: R itself for FP32 states, the adjoint type for
+// FP64 states).
+template <class RF>
 struct CollideTape {
-    RT drho, jx, jy, irho, ux, uy, Fx, Fy, T;
-    RT gX[3][3], gN[3][3], gT[3][3], gY[3][3];   // energy: line inputs, central, relaxed, inverse
-    RT fX[3][3], fD[3][3], fT[3][3], fY[3][3];   // flow (deviations): the same four stages
+    RF drho, jx, jy, irho, ux, uy, Fx, Fy, T;
+    RF gX[3][3], gN[3][3], gT[3][3], gY[3][3];   // energy: line inputs, central, relaxed, inverse
+    RF fX[3][3], fD[3][3], fT[3][3], fY[3][3];   // flow (deviations): the same four stages
 };
 
-template <class RF, class RT>
-__device__ __forceinline__ void collide_forward_tape(const RF pf[9], const RF pg[9],
-                                                     const Coeffs2D<RF>& c, CollideTape<RT>& tp)
+template <class R, class RF>
+__device__ __forceinline__ void collide_forward_tape(const R pf[9], const R pg[9],
+                                                     const Coeffs2D<R>& c, CollideTape<RF>& tp)
 {
-    const RF half = RF(0.5);
-    RF dT = 0, drho = 0, jx = 0, jy = 0;
+    const R half = R(0.5);
+    R dT = 0, drho = 0, jx = 0, jy = 0;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
         dT += pg[a];
         drho += pf[a];
-        jx += pf[a] * RF(e9(a, 0));
-        jy += pf[a] * RF(e9(a, 1));
+        jx += pf[a] * R(e9(a, 0));
+        jy += pf[a] * R(e9(a, 1));
     }
-    const RF Fb = c.gbeta * dT;
-    const RF Fx = c.gaxis == 0 ? Fb : RF(0), Fy = c.gaxis == 1 ? Fb : RF(0);
-    const RF rho = RF(1) + drho, irho = RF(1) / rho;
-    const RF ux = (jx + half * Fx) * irho, uy = (jy + half * Fy) * irho;
-    const RF T = c.T_ref + dT;
-    tp.drho = RT(drho); tp.jx = RT(jx); tp.jy = RT(jy); tp.irho = RT(irho);
-    tp.ux = RT(ux); tp.uy = RT(uy); tp.Fx = RT(Fx); tp.Fy = RT(Fy); tp.T = RT(T);
-    auto keep = [](const RF in[3][3], RT out[3][3]) {
+    const R Fb = c.gbeta * dT;
+    const R Fx = c.gaxis == 0 ? Fb : R(0), Fy = c.gaxis == 1 ? Fb : R(0);
+    const R rho = R(1) + drho, irho = R(1) / rho;
+    const R ux = (jx + half * Fx) * irho, uy = (jy + half * Fy) * irho;
+    const R T = c.T_ref + dT;
+    tp.drho = RF(drho); tp.jx = RF(jx); tp.jy = RF(jy); tp.irho = RF(irho);
+    tp.ux = RF(ux); tp.uy = RF(uy); tp.Fx = RF(Fx); tp.Fy = RF(Fy); tp.T = RF(T);
+    auto keep = [](const R in[3][3], RF out[3][3]) {
 #pragma unroll
         for (int j = 0; j < 3; ++j)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) out[j][a] = RT(in[j][a]);
+            for (int a = 0; a < 3; ++a) out[j][a] = RF(in[j][a]);
     };
     {
-        RF gin[9];
+        R gin[9];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) gin[a] = pg[a] + RF(w9(a)) * c.T_ref;
-        RF X[3][3], N[3][3], Tm[3][3], Y[3][3];
+        for (int a = 0; a < 9; ++a) gin[a] = pg[a] + R(w9(a)) * c.T_ref;
+        R X[3][3], N[3][3], Tm[3][3], Y[3][3];
         sweeps_fwd(gin, X, N, ux, uy);
         keep(X, tp.gX);
         keep(N, tp.gN);
@@ -349,7 +387,7 @@ __device__ __forceinline__ void collide_forward_tape(const RF pf[9], const RF pg
         keep(Y, tp.gY);
     }
     {
-        RF X[3][3], D[3][3], Tm[3][3], Y[3][3];
+        R X[3][3], D[3][3], Tm[3][3], Y[3][3];
         sweeps_fwd(pf, X, D, ux, uy);
         keep(X, tp.fX);
         keep(D, tp.fD);
@@ -366,14 +404,15 @@ __device__ __forceinline__ void collide_forward_tape(const RF pf[9], const RF pg
 
 // Vector-Jacobian product of the node collision at the forward values tp: adjoints of the
 // post-collision deviations (lf, lg) -> adjoints of the pulled deviations (mf, mg), in RT.
-template <class RT, bool kSync = false>
-__device__ __forceinline__ void collide_vjp_d2q9(const CollideTape<RT>& tp, const RT lf[9],
-                                                 const RT lg[9], const Coeffs2D<RT>& c, RT mf[9],
+// kSync: a block-wide barrier between the energy and the flow products (see the kernel).
+template <class RT, class RF, bool kSync = false>
+__device__ __forceinline__ void collide_vjp_d2q9(const CollideTape<RF>& tp, const RT lf[9],
+                                                 const RT lg[9], const Coeffs2D<RF>& c, RT mf[9],
                                                  RT mg[9])
 {
-    const RT half = RT(0.5);
-    const RT drho = tp.drho, jx = tp.jx, jy = tp.jy, irho = tp.irho, ux = tp.ux, uy = tp.uy;
-    const RT Fx = tp.Fx, Fy = tp.Fy, T = tp.T;
+    const RF half = RF(0.5);
+    const RF drho = tp.drho, jx = tp.jx, jy = tp.jy, irho = tp.irho, ux = tp.ux, uy = tp.uy;
+    const RF Fx = tp.Fx, Fy = tp.Fy, T = tp.T;
 
     RT uxb = 0, uyb = 0, drhob = 0, irhob = 0, Fxb = 0, Fyb = 0, dTb = 0;
 
@@ -395,29 +434,40 @@ __device__ __forceinline__ void collide_vjp_d2q9(const CollideTape<RT>& tp, cons
         sweeps_vjp(tp.fX, tp.fD, Db, ux, uy, mf, uxb, uyb);
     }
     // macroscopic fields: u = (j + F/2) irho, irho = 1 / (1 + drho), F = g beta dT along gravity
-    const RT jxb = uxb * irho, jyb = uyb * irho;
-    Fxb += half * uxb * irho;
-    Fyb += half * uyb * irho;
-    irhob += uxb * (jx + half * Fx) + uyb * (jy + half * Fy);
-    drhob += -irhob * irho * irho;
-    const RT Fbb = (c.gaxis == 0 ? Fxb : RT(0)) + (c.gaxis == 1 ? Fyb : RT(0));
-    dTb += c.gbeta * Fbb;
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        mf[a] += drhob + jxb * RT(e9(a, 0)) + jyb * RT(e9(a, 1));
+    const RT jxb = am(uxb, irho), jyb = am(uyb, irho);
+    Fxb += am(uxb, half * irho);
+    Fyb += am(uyb, half * irho);
+    irhob += am(uxb, jx + half * Fx) + am(uyb, jy + half * Fy);
+    drhob -= am(irhob, irho * irho);
+    const RT Fbb = c.gaxis == 0 ? Fxb : (c.gaxis == 1 ? Fyb : RT(0));
+    dTb += am(Fbb, c.gbeta);
+    static_for<9>([&](auto I) {
+        constexpr int a = decltype(I)::value;
+        RT m = drhob;
+        if constexpr (e9(a, 0) == 1) m += jxb;
+        if constexpr (e9(a, 0) == -1) m -= jxb;
+        if constexpr (e9(a, 1) == 1) m += jyb;
+        if constexpr (e9(a, 1) == -1) m -= jyb;
+        mf[a] += m;
         mg[a] += dTb;
-    }
+    });
 }
 
-// First fixed-temperature face crossed by the link arriving along (EX, EY) at a node with walls w
-// (the face whose temperature the anti-bounce-back uses), or -1.
+// The fixed-temperature face whose anti-bounce-back the link arriving along (EX, EY) at a node
+// with walls w takes (the crossed face of highest face_rank, when it is a fixed-T face), or -1.
 template <int EX, int EY, class R>
 __device__ __forceinline__ int first_fixed_face(const NodeWalls<R>& w)
 {
-    if (EX == 1 && w.fix_m[0]) return 0;
-    if (EX == -1 && w.fix_p[0]) return 1;
-    if (EY == 1 && w.fix_m[1]) return 2;
-    if (EY == -1 && w.fix_p[1]) return 3;
+    const bool cx = EX == 1 ? w.out_m[0] : (EX == -1 ? w.out_p[0] : false);
+    const bool cy = EY == 1 ? w.out_m[1] : (EY == -1 ? w.out_p[1] : false);
+    const int fx = EX == 1 ? 0 : 1, fy = EY == 1 ? 2 : 3;
+    const bool fix_x = EX == 1 ? w.fix_m[0] : (EX == -1 ? w.fix_p[0] : false);
+    const bool fix_y = EY == 1 ? w.fix_m[1] : (EY == -1 ? w.fix_p[1] : false);
+    // the y face outranks the x face for EY = -1 (the +y face); the x face outranks -y
+    const bool y_first = EY == -1;
+    if (y_first && cy) return fix_y ? fy : -1;
+    if (cx) return fix_x ? fx : -1;
+    if (cy) return fix_y ? fy : -1;
     return -1;
 }
 
@@ -433,10 +483,11 @@ __global__ void __launch_bounds__(kSync ? 256 : 128, kSync ? 2 : 1)
     adjoint_step_d2q9_kernel(const typename S::T* __restrict__ f_prev,
                              const typename S::T* __restrict__ g_prev,
                              const RT* __restrict__ mu_in, RT* __restrict__ mu_out, Geometry geo,
-                             Coeffs2D<typename S::R> cr, Coeffs2D<RT> c, int design_face,
-                             double* __restrict__ grad)
+                             Coeffs2D<typename S::R> cr, Coeffs2D<TapeT<typename S::R, RT>> c,
+                             int design_face, double* __restrict__ grad)
 {
     using R = typename S::R;
+    using RF = TapeT<R, RT>;
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     const bool active = x < geo.nx && y < geo.ny;
@@ -469,11 +520,11 @@ __global__ void __launch_bounds__(kSync ? 256 : 128, kSync ? 2 : 1)
     // forward pull of p_k from s_{k-1}
     R fr[9], gr[9];
     pull_d2q9<S, size_t>(f_prev, g_prev, geo, w, i, cr.T_ref, fr, gr);
-    CollideTape<RT> tape;
+    CollideTape<RF> tape;
     collide_forward_tape(fr, gr, cr, tape);
     if constexpr (kSync) __syncthreads();
     RT mf[9], mg[9];
-    collide_vjp_d2q9<RT, kSync>(tape, lf, lg, c, mf, mg);
+    collide_vjp_d2q9<RT, RF, kSync>(tape, lf, lg, c, mf, mg);
     if (!active) return;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {

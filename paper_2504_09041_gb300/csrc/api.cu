@@ -279,6 +279,7 @@ int plan_box(int lattice, int nx, int ny, int nz, double Ra, double Pr, double M
     hc.T_ref = bc->T_ref;
     hc.gaxis = bc->gravity_axis;
     hc.fp16_sr = 1;
+    hc.adj_sync = 2;   // adjoint step: 128 x 2 blocks with phase barriers (measured fastest)
     const double om_nu = 1.0 / (3.0 * P->nu + 0.5);
     const double om_alpha = 1.0 / (3.0 * P->alpha + 0.5);
     // App. A, B, C: shear / diffusivity rates from nu / alpha, bulk and every free rate 1
@@ -455,15 +456,9 @@ int lbm_set_param(lbm_handle h, const char* key, double v)
         return LBM_OK;
     }
     if (k == "adjoint_sync") {
-        if (!(v == 0.0 || v == 1.0 || v == 2.0)) return fail(h, LBM_EINVAL, "adjoint_sync must be 0, 1 or 2");
+        if (!(v == 0.0 || v == 1.0 || v == 2.0 || v == 3.0 || v == 4.0))
+            return fail(h, LBM_EINVAL, "adjoint_sync must be 0 (64x2 blocks) or 1-4 (64x4, 128x2, 32x4, 64x2 with phase barriers)");
         h->hc.adj_sync = (int)v;
-        return LBM_OK;
-    }
-    if (k == "l2_prefetch") {
-        const int v_i = (int)v;
-        if (v != (double)v_i || v_i < 0 || v_i > (1 << 24))
-            return fail(h, LBM_EINVAL, "l2_prefetch must be an integer in [0, 2^24] (blocks ahead)");
-        h->hc.l2_pf = v_i;
         return LBM_OK;
     }
     if (k == "fp16_stochastic") {

@@ -34,8 +34,8 @@ struct HostCoeffs {
     int gopt;   // energy attractors of orders 3-4: 0 = option A, 1 = option B
     int fp16_sr;   // F16S storage: stochastic (1) or nearest (0) rounding of stored deviations
     int index64;   // 1: the step uses 64-bit element offsets even where 32-bit ones suffice
-    int l2_pf;     // 3D step: blocks ahead whose input rows each block prefetches into L2 (0: off)
-    int adj_sync;  // adjoint step: 0 = 64x2 blocks; 1 = 64x4, 2 = 128x2 blocks with phase barriers
+    int adj_sync;  // adjoint step blocks: 0 = 64x2; with phase barriers 1 = 64x4, 2 = 128x2 (default),
+                   // 3 = 32x4, 4 = 64x2
 };
 
 size_t storage_bytes(int prec);
@@ -140,7 +140,6 @@ inline Coeffs<R, QF, QG> make_coeffs(const HostCoeffs& h)
     c.gaxis = h.gaxis;
     c.gopt = h.gopt;
     c.fp16_sr = h.fp16_sr;
-    c.l2_pf = h.l2_pf;
     return c;
 }
 

@@ -132,7 +132,6 @@ struct Coeffs {
     int gaxis;    // 0, 1, 2
     int gopt;     // energy attractors of orders 3-4: 0 = option A, 1 = option B (renormalized)
     int fp16_sr;  // F16S storage: 1 = stochastic rounding of the stored deviations, 0 = nearest
-    int l2_pf;    // 3D step: L2 prefetch of the input rows of the block this many blocks ahead (0: off)
 };
 
 // Per-thread wall bookkeeping for the pull.  For an axis, "m" is a link whose source lies at
@@ -204,26 +203,53 @@ __device__ __forceinline__ NodeWalls<R> node_walls_x(const Geometry& g, int x, i
     return w;
 }
 
+// Order of the faces for links that cross two or three walls at an edge or corner of the box:
+// the crossed face latest in the order -z, -y, -x, +x, +y, +z (the order of the neighbours'
+// linear indices) decides the link's rule.  rank(axis, c) of the face that a link with component
+// c = +1 (source at coordinate - 1: the - face) or c = -1 (the + face) crosses on that axis.
+__host__ __device__ constexpr int face_rank(int ax, int c)
+{
+    return c == 1 ? 2 - ax : 3 + ax;
+}
+
 // Source of the link arriving at node i along (EX, EY, EZ) after the walls.  Returns the
-// linear index of the source node.  *out is set when the source lies beyond a wall; *dir is
-// set when one of the crossed walls has a fixed temperature, and *tw is then the temperature of
-// the first such face in the order -x, +x, -y, +y, -z, +z.
+// linear index of the source node.  *out is set when the source lies beyond a wall.  The crossed
+// wall that decides the rule is the one of highest face_rank: *dir is set when it has a fixed
+// temperature (anti-bounce-back), and *tw is then its temperature; otherwise the link bounces
+// back.  Faces crossed by an edge or corner link therefore decide in the order above.
 template <int EX, int EY, int EZ, class R>
 __device__ __forceinline__ int link_source(const Geometry& g, const NodeWalls<R>& w, int i,
                                            bool* out, bool* dir, R* tw)
 {
     int s = i - (EX + EY * g.nx + EZ * g.nxy);
-    bool o = false, d = false;
+    bool o = false;
+    if (EX == 1) { s += w.wrap_m[0]; o |= w.out_m[0]; }
+    if (EX == -1) { s += w.wrap_p[0]; o |= w.out_p[0]; }
+    if (EY == 1) { s += w.wrap_m[1]; o |= w.out_m[1]; }
+    if (EY == -1) { s += w.wrap_p[1]; o |= w.out_p[1]; }
+    if (EZ == 1) { s += w.wrap_m[2]; o |= w.out_m[2]; }
+    if (EZ == -1) { s += w.wrap_p[2]; o |= w.out_p[2]; }
+    // the deciding face: visit the crossed axes from the highest face rank down
+    bool decided = false, d = false;
     R t = R(0);
-    if (EX == 1) { s += w.wrap_m[0]; o |= w.out_m[0]; if (w.fix_m[0]) { d = true; t = w.tw_m[0]; } }
-    if (EX == -1) { s += w.wrap_p[0]; o |= w.out_p[0]; if (w.fix_p[0]) { d = true; t = w.tw_p[0]; } }
-    if (EY == 1) { s += w.wrap_m[1]; o |= w.out_m[1]; if (w.fix_m[1] && !d) { d = true; t = w.tw_m[1]; } }
-    if (EY == -1) { s += w.wrap_p[1]; o |= w.out_p[1]; if (w.fix_p[1] && !d) { d = true; t = w.tw_p[1]; } }
-    if (EZ == 1) { s += w.wrap_m[2]; o |= w.out_m[2]; if (w.fix_m[2] && !d) { d = true; t = w.tw_m[2]; } }
-    if (EZ == -1) { s += w.wrap_p[2]; o |= w.out_p[2]; if (w.fix_p[2] && !d) { d = true; t = w.tw_p[2]; } }
+    constexpr int e[3] = {EX, EY, EZ};
+#pragma unroll
+    for (int r = 5; r >= 0; --r) {
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            if (e[ax] == 0 || face_rank(ax, e[ax]) != r) continue;
+            const bool crossed = e[ax] == 1 ? w.out_m[ax] : w.out_p[ax];
+            const bool fixed = e[ax] == 1 ? w.fix_m[ax] : w.fix_p[ax];
+            if (crossed && !decided) {
+                decided = true;
+                d = fixed;
+                t = e[ax] == 1 ? w.tw_m[ax] : w.tw_p[ax];
+            }
+        }
+    }
     *out = o;
     *dir = d;
-    *tw = t;
+    *tw = d ? t : R(0);
     return s;
 }
 

@@ -571,41 +571,6 @@ __device__ __forceinline__ void collide_store_d3q27(typename S::R f[27], typenam
     });
 }
 
-// L2 prefetch for a block further ahead in launch order.  Block B prefetches, into L2, the rows of
-// all 42 input population planes that block B + ahead updates.  Those rows are what B + ahead and
-// its y and z neighbours (one row or one plane apart, about 1024 blocks at 256^3) pull, so with
-// `ahead` beyond a plane of blocks the pull of every block finds its upwind rows in L2 instead of
-// waiting on DRAM.  The prefetches are fire-and-forget (no registers or scoreboard wait); the
-// bytes fetched are the same ones the step reads anyway.
-template <class S>
-__device__ __forceinline__ void prefetch_ahead_d3q27(const typename S::T* __restrict__ fin,
-                                                     const typename S::T* __restrict__ gin,
-                                                     const Geometry& geo, int ahead)
-{
-    using T = typename S::T;
-    const unsigned long long nb = (unsigned long long)gridDim.x * gridDim.y * gridDim.z;
-    const unsigned long long lin = blockIdx.x + (unsigned long long)gridDim.x * (blockIdx.y + (unsigned long long)gridDim.y * blockIdx.z);
-    const unsigned long long fut = lin + (unsigned)ahead;
-    if (fut >= nb) return;
-    const int fbx = (int)(fut % gridDim.x);
-    const int fby = (int)((fut / gridDim.x) % gridDim.y);
-    const int fbz = (int)(fut / ((unsigned long long)gridDim.x * gridDim.y));
-    const int x0 = fbx * blockDim.x, y0 = fby * blockDim.y;
-    const int cnt = min((int)blockDim.x, geo.nx - x0);    // nodes of each row
-    if (cnt <= 0) return;
-    const int rows = min((int)blockDim.y, geo.ny - y0);
-    const int bytes = cnt * (int)sizeof(T);
-    const int tid = threadIdx.x + blockDim.x * threadIdx.y, nthr = blockDim.x * blockDim.y;
-    for (int k = tid; k < 42 * rows; k += nthr) {
-        const int a = k % 42, r = k / 42;
-        const size_t node = (size_t)x0 + (size_t)geo.nx * (y0 + r) + (size_t)geo.nxy * fbz;
-        const char* p = reinterpret_cast<const char*>(a < 27 ? fin + (size_t)a * geo.n + node
-                                                              : gin + (size_t)(a - 27) * geo.n + node);
-        for (int o = 0; o < bytes; o += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + o));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(p + bytes - 1));
-    }
-}
-
 template <class S>
 struct Launch3D {
     static constexpr int kMinBlocks = sizeof(typename S::R) == 8 ? 1 : 3;
@@ -617,7 +582,6 @@ __global__ void __launch_bounds__(256, LBM_MINB3D)
                       typename S::T* __restrict__ fout, typename S::T* __restrict__ gout,
                       Geometry geo, Coeffs3D<typename S::R> c, unsigned* status)
 {
-    if (c.l2_pf > 0) prefetch_ahead_d3q27<S>(fin, gin, geo, c.l2_pf);
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;

@@ -523,3 +523,64 @@ def test_transport_mapping_matches_worked_numbers():
     assert tr.gbeta * 1.0 * 64 == pytest.approx(tr.U ** 2)
     # Ra recovered from the definition of Sec. 6.1
     assert tr.gbeta * 1.0 * 64 ** 3 / (tr.alpha * tr.nu) == pytest.approx(1e4)
+
+
+# ---------------------------------------------------------------------------------------------
+# Walls at edges and corners (reading R7)
+# ---------------------------------------------------------------------------------------------
+
+# Order in which the faces -x, +x, -y, +y, -z, +z decide a link that crosses several walls
+# (reading R7: the crossed face that comes last in the order -z, -y, -x, +x, +y, +z).
+R7_ORDER = ("-z", "-y", "-x", "+x", "+y", "+z")
+FACE_NAMES = ("-x", "+x", "-y", "+y", "-z", "+z")
+
+
+def pulled_T_by_hand(dim, g, kinds, T_wall, E, W, x, y, z):
+    """T at node (x, y, z) after streaming, written out link by link: a link whose upwind node
+    lies inside takes that node's population; one whose upwind node lies beyond walls takes the
+    rule of the deciding face (R7_ORDER): bounce-back g_abar(x) at an adiabatic face,
+    anti-bounce-back -g_abar(x) + 2 w_a T_w at a fixed-temperature face."""
+    q, nz, ny, nx = g.shape
+    ext = (nx, ny, nz)
+    c = (x, y, z)
+    T = 0.0
+    for a in range(q):
+        e = E[a]
+        opp = [b for b in range(q) if all(E[b][d] == -e[d] for d in range(3))][0]
+        src = [c[d] - e[d] for d in range(3)]
+        crossed = []
+        for d in range(dim):
+            if src[d] < 0:
+                crossed.append(2 * d)
+            elif src[d] >= ext[d]:
+                crossed.append(2 * d + 1)
+        if not crossed:
+            T += g[a, src[2], src[1], src[0]]
+            continue
+        face = max(crossed, key=lambda f: R7_ORDER.index(FACE_NAMES[f]))
+        back = g[opp, z, y, x]
+        T += -back + 2.0 * W[a] * T_wall[face] if kinds[face] == O.WALL_FIXED_T else back
+    return T
+
+
+@pytest.mark.parametrize("dim,shape", [(2, (1, 3, 3)), (3, (3, 3, 3)), (3, (3, 4, 2))])
+def test_edge_and_corner_links_follow_reading_r7(dim, shape):
+    """Every node of a box two to four nodes wide (so that every node is an edge or corner node
+    of the cavity: hot -x, cold +x, adiabatic elsewhere): the oracle's streamed temperature equals
+    the link-by-link sum of the walls' rules, with edge and corner links decided as reading R7
+    states.  A random state makes every link's contribution distinct."""
+    nz, ny, nx = shape
+    bc = O.cavity_bc(dim, T_hot=1.0, T_cold=0.0)
+    o = O.Oracle(dim, nx, ny, nz, bc=bc, Ra=1e4, Pr=0.71, Ma=0.1)
+    rng = np.random.default_rng(40 + dim)
+    f, g = o.get_state()
+    g = g * rng.uniform(0.5, 1.5, g.shape)
+    o.set_state(f, g)
+    E = O.E_D2Q9 if dim == 2 else O.E_D3Q15
+    W = O.equilibrium_g(dim, 1.0)
+    T = o.fields()["T"]
+    for z in range(o.nz):
+        for y in range(ny):
+            for x in range(nx):
+                want = pulled_T_by_hand(dim, g, bc.face, bc.T_wall, E, W, x, y, z)
+                assert T[z, y, x] == pytest.approx(want, abs=1e-14), (x, y, z)
