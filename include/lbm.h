@@ -141,7 +141,9 @@ LBM_API int lbm_set_omegas(lbm_handle h, const double* om_f, int n_f, const doub
  * "adjoint_sync" (thread blocks of the adjoint kernel: 0 = 64 x 2; 1-4 = 64 x 4, 128 x 2 (the
  * default), 32 x 4, 64 x 2 whose warps pass a barrier between the phases of the node's work so
  * that they share the instruction fetches of the long unrolled product; results agree to
- * rounding),
+ * rounding), "adjoint_overlap" (1, the default: lbm_adjoint_step recomputes the next segment's
+ * states on a second, low-priority stream while the adjoint steps of the current one run, with
+ * a second set of segment buffers; 0: one stream, one set),
  * "graph_steps" (even count of steps that lbm_step replays as one CUDA graph; 0 disables),
  * "index64" (1: the step kernels use 64-bit element offsets, the instantiation that boxes with
  * q n >= 2^32 run, on any box; results are bitwise those of the 32-bit form; for testing that path), or the

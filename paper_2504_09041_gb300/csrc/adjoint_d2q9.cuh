@@ -70,9 +70,15 @@ __device__ __forceinline__ void central_line_vjp(RF k0, RF k1, RF u, RT K0, RT K
     const RT Db = K1t - uK2;           // adjoint of d; K2 is the adjoint of s = c + a
     const RT K0t = K0 - am(K1t, u);    // total adjoint of k0
     ubar -= am(K2, d + k1) + am(K1t, k0);
-    Ab = (K0t - Db) + K2;
+    if constexpr (std::is_same<RT, dfloat>::value) {
+        const RT P = K0t + K2;     // one double-float sum fewer
+        Ab = P - Db;
+        Cb = P + Db;
+    } else {
+        Ab = (K0t - Db) + K2;
+        Cb = (K0t + Db) + K2;
+    }
     Bb = K0t;
-    Cb = (K0t + Db) + K2;
 }
 
 // Reverse of uncentral_line: inputs (k0, k1, k2) at velocity u, adjoints (Ab, Bb, Cb) of the

@@ -52,6 +52,7 @@ struct lbm_s {
     cudaStream_t stream = nullptr;
     int block_x = 0, block_y = 0;   // launch shape of the step kernel (0: default)
     int adjoint_arith = 2;          // arithmetic of the adjoint's VJPs: 0 FP32, 1 FP64, 2 double-float
+    int adjoint_overlap = 1;        // recompute the next segment on a second stream beside the adjoint steps
     int tma_rows = 0;               // 3D FP32/FP16S: TMA-staged step with tiles of 64 x tma_rows
     lbm::TmaMaps tm[2];             // tensor maps of the input buffers f[c], g[c]
     // CUDA graphs of graph_steps consecutive steps (even, so the A/B parity returns), one per
@@ -60,6 +61,7 @@ struct lbm_s {
     unsigned gen = 1, graph_gen[2] = {0, 0};
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     cudaStream_t capture_stream = nullptr;
+    cudaStream_t aux_stream = nullptr;   // adjoint: recompute of the next segment, beside the adjoint steps
     long long steps = 0;
     std::string err;
     lbm_alloc_fn alloc = nullptr;
@@ -103,6 +105,10 @@ void release(lbm_s* h)
     for (int k = 0; k < 2; ++k)
         if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    if (h->aux_stream) {
+        cudaStreamSynchronize(h->aux_stream);
+        cudaStreamDestroy(h->aux_stream);
+    }
     for (int k = 0; k < 2; ++k) {
         dev_free(h, h->f[k]);
         dev_free(h, h->g[k]);
@@ -455,6 +461,11 @@ int lbm_set_param(lbm_handle h, const char* key, double v)
         h->hc.index64 = (int)v;
         return LBM_OK;
     }
+    if (k == "adjoint_overlap") {
+        if (!(v == 0.0 || v == 1.0)) return fail(h, LBM_EINVAL, "adjoint_overlap must be 0 or 1");
+        h->adjoint_overlap = (int)v;
+        return LBM_OK;
+    }
     if (k == "adjoint_sync") {
         if (!(v == 0.0 || v == 1.0 || v == 2.0 || v == 3.0 || v == 4.0))
             return fail(h, LBM_EINVAL, "adjoint_sync must be 0 (64x2 blocks) or 1-4 (64x4, 128x2, 32x4, 64x2 with phase barriers)");
@@ -723,19 +734,33 @@ int lbm_adjoint_step(lbm_handle h, long n_steps, int objective_face, int design_
     const size_t fb = (size_t)h->qf * h->geo.n * sb, gb = (size_t)h->qg * h->geo.n * sb;
     const long K = (long)std::ceil(std::sqrt((double)n_steps));
     const long nck = (n_steps + K - 1) / K;
-    // device memory: nck checkpoints, K segment states, two adjoint buffers, the gradient
-    std::vector<void*> ckf(nck, nullptr), ckg(nck, nullptr), sgf(K, nullptr), sgg(K, nullptr);
+    // device memory: nck checkpoints, two sets of K segment states, two adjoint buffers, the
+    // gradient.  Segment m's states are recomputed into one set while the adjoint steps of
+    // segment m + 1 read the other (on a second stream, so the two overlap on the GPU).
+    std::vector<void*> ckf(nck, nullptr), ckg(nck, nullptr);
+    std::vector<void*> sgf_[2] = {std::vector<void*>(K, nullptr), std::vector<void*>(K, nullptr)};
+    std::vector<void*> sgg_[2] = {std::vector<void*>(K, nullptr), std::vector<void*>(K, nullptr)};
     void* mu[2] = {nullptr, nullptr};
     double* grad = nullptr;
     const int arith = h->adjoint_arith;
-    cudaGraphExec_t seg_exec = nullptr;
+    cudaGraphExec_t seg_exec[2] = {nullptr, nullptr};
+    // the K adjoint steps of a full segment of set s starting on adjoint buffer a: adj_exec[s][a]
+    cudaGraphExec_t adj_exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
     auto cleanup = [&]() {
         cudaStreamSynchronize(h->stream);
-        if (seg_exec) cudaGraphExecDestroy(seg_exec);
+        if (h->aux_stream) cudaStreamSynchronize(h->aux_stream);
+        for (int s = 0; s < 2; ++s) {
+            if (seg_exec[s]) cudaGraphExecDestroy(seg_exec[s]);
+            for (int b = 0; b < 2; ++b)
+                if (adj_exec[s][b]) cudaGraphExecDestroy(adj_exec[s][b]);
+            if (ev_rec[s]) cudaEventDestroy(ev_rec[s]);
+            if (ev_free[s]) cudaEventDestroy(ev_free[s]);
+            for (auto p : sgf_[s]) dev_free(h, p);
+            for (auto p : sgg_[s]) dev_free(h, p);
+        }
         for (auto p : ckf) dev_free(h, p);
         for (auto p : ckg) dev_free(h, p);
-        for (auto p : sgf) dev_free(h, p);
-        for (auto p : sgg) dev_free(h, p);
         dev_free(h, mu[0]);
         dev_free(h, mu[1]);
         dev_free(h, grad);
@@ -744,7 +769,11 @@ int lbm_adjoint_step(lbm_handle h, long n_steps, int objective_face, int design_
     for (long m = 0; m < nck && ok; ++m) ok = (ckf[m] = dev_alloc(h, fb)) && (ckg[m] = dev_alloc(h, gb));
     // segment states 1 .. K-1, and state 0: the copy of a checkpoint that the recompute graph reads
     const bool seg_graph = K >= 3;
-    for (long r = seg_graph ? 0 : 1; r < K && ok; ++r) ok = (sgf[r] = dev_alloc(h, fb)) && (sgg[r] = dev_alloc(h, gb));
+    // the second set only when another full segment precedes the last one
+    const int nsets = seg_graph && nck >= 2 && h->adjoint_overlap ? 2 : 1;
+    for (int s = 0; s < nsets; ++s)
+        for (long r = seg_graph ? 0 : 1; r < K && ok; ++r)
+            ok = (sgf_[s][r] = dev_alloc(h, fb)) && (sgg_[s][r] = dev_alloc(h, gb));
     const size_t mub = (size_t)(h->qf + h->qg) * h->geo.n * (arith == lbm::kAdjF32 ? sizeof(float) : 8);
     ok = ok && (mu[0] = dev_alloc(h, mub)) && (mu[1] = dev_alloc(h, mub)) &&
          (grad = (double*)dev_alloc(h, sizeof(double) * n));
@@ -789,50 +818,107 @@ int lbm_adjoint_step(lbm_handle h, long n_steps, int objective_face, int design_
     ADJ_CK(cudaMemsetAsync(mu[a], 0, mub, h->stream));
     ADJ_CK(cudaMemsetAsync(grad, 0, sizeof(double) * n, h->stream));
     ADJ_CK(lbm::launch_adjoint_seed(h->geo, objective_face, scale, mu[a], arith, h->stream));
-    // The K - 1 recompute steps of a full segment, state 0 -> 1 -> ... -> K - 1 of the segment
-    // buffers, captured once as a CUDA graph; each full segment copies its checkpoint into state 0
-    // and replays it.
+    // The K - 1 recompute steps of a full segment, state 0 -> 1 -> ... -> K - 1 of one set of
+    // segment buffers, captured once per set as a CUDA graph; each full segment copies its
+    // checkpoint into state 0 of its set and replays that set's graph.
     if (seg_graph) {
         if (!h->capture_stream) ADJ_CK(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
-        cudaGraph_t g = nullptr;
-        ADJ_CK(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = cudaSuccess;
-        for (long r2 = 1; r2 < K && e == cudaSuccess; ++r2)
-            e = lbm::launch_step(h->dim, h->prec, sgf[r2 - 1], sgg[r2 - 1], sgf[r2], sgg[r2], h->geo, h->hc,
-                                 h->status, blk, h->capture_stream);
-        const cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
-        if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&seg_exec, g, 0);
-        if (g) cudaGraphDestroy(g);
-        ADJ_CK(e != cudaSuccess ? e : e2);
+        for (int s = 0; s < nsets; ++s) {
+            cudaGraph_t g = nullptr;
+            ADJ_CK(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (long r2 = 1; r2 < K && e == cudaSuccess; ++r2)
+                e = lbm::launch_step(h->dim, h->prec, sgf_[s][r2 - 1], sgg_[s][r2 - 1], sgf_[s][r2],
+                                     sgg_[s][r2], h->geo, h->hc, h->status, blk, h->capture_stream);
+            const cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
+            if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&seg_exec[s], g, 0);
+            if (g) cudaGraphDestroy(g);
+            ADJ_CK(e != cudaSuccess ? e : e2);
+        }
     }
-    // backward over the segments, last first
+    if (nsets == 2) {
+        if (!h->aux_stream) {
+            // the lowest priority: the block scheduler prefers the adjoint steps' blocks
+            int least = 0, greatest = 0;
+            ADJ_CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+            ADJ_CK(cudaStreamCreateWithPriority(&h->aux_stream, cudaStreamNonBlocking, least));
+        }
+        for (int s = 0; s < 2; ++s) {
+            ADJ_CK(cudaEventCreateWithFlags(&ev_rec[s], cudaEventDisableTiming));
+            ADJ_CK(cudaEventCreateWithFlags(&ev_free[s], cudaEventDisableTiming));
+        }
+        // the aux stream starts after everything queued so far (checkpoints, seed)
+        ADJ_CK(cudaEventRecord(ev_free[1], h->stream));
+        ADJ_CK(cudaStreamWaitEvent(h->aux_stream, ev_free[1], 0));
+    }
+    // Recompute of full segment m into set s on stream st: its checkpoint into state 0, then the
+    // set's graph.
+    auto recompute_full = [&](long m, int s, cudaStream_t st) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(sgf_[s][0], ckf[m], fb, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sgg_[s][0], ckg[m], gb, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaGraphLaunch(seg_exec[s], st);
+        return e;
+    };
+    // backward over the segments, last first; segment m uses set (nck - 1 - m) % 2
     for (long m = nck - 1; m >= 0; --m) {
+        const int s = nsets == 2 ? (int)((nck - 1 - m) % 2) : 0;
         const long lo = m * K, hi = std::min((m + 1) * K, n_steps);
         std::vector<const void*> sf(hi - lo), sg(hi - lo);
         sf[0] = ckf[m];
         sg[0] = ckg[m];
         if (seg_graph && hi - lo == K) {
-            ADJ_CK(cudaMemcpyAsync(sgf[0], ckf[m], fb, cudaMemcpyDeviceToDevice, h->stream));
-            ADJ_CK(cudaMemcpyAsync(sgg[0], ckg[m], gb, cudaMemcpyDeviceToDevice, h->stream));
-            ADJ_CK(cudaGraphLaunch(seg_exec, h->stream));
+            if (m == nck - 1 || nsets == 1) ADJ_CK(recompute_full(m, s, h->stream));
+            else ADJ_CK(cudaStreamWaitEvent(h->stream, ev_rec[s], 0));   // recomputed on the aux stream
             for (long r2 = 1; r2 < K; ++r2) {
-                sf[r2] = sgf[r2];
-                sg[r2] = sgg[r2];
+                sf[r2] = sgf_[s][r2];
+                sg[r2] = sgg_[s][r2];
             }
         } else {
             for (long r2 = 1; r2 < hi - lo; ++r2) {
-                ADJ_CK(lbm::launch_step(h->dim, h->prec, sf[r2 - 1], sg[r2 - 1], sgf[r2], sgg[r2], h->geo,
-                                        h->hc, h->status, blk, h->stream));
-                sf[r2] = sgf[r2];
-                sg[r2] = sgg[r2];
+                ADJ_CK(lbm::launch_step(h->dim, h->prec, sf[r2 - 1], sg[r2 - 1], sgf_[s][r2], sgg_[s][r2],
+                                        h->geo, h->hc, h->status, blk, h->stream));
+                sf[r2] = sgf_[s][r2];
+                sg[r2] = sgg_[s][r2];
             }
         }
-        for (long k = hi; k >= lo + 1; --k) {
-            ADJ_CK(lbm::launch_adjoint_step_d2q9(h->prec, arith, sf[k - 1 - lo], sg[k - 1 - lo], mu[a],
-                                                 mu[1 - a], h->geo, h->hc, design_face, grad,
-                                                 h->stream));
-            a = 1 - a;
+        // segment m - 1 (always full) into the other set, beside this segment's adjoint steps, once
+        // the adjoint steps of segment m + 1, which read that set, are done
+        if (nsets == 2 && m >= 1) {
+            if (m + 1 <= nck - 1) ADJ_CK(cudaStreamWaitEvent(h->aux_stream, ev_free[1 - s], 0));
+            ADJ_CK(recompute_full(m - 1, 1 - s, h->aux_stream));
+            ADJ_CK(cudaEventRecord(ev_rec[1 - s], h->aux_stream));
         }
+        if (seg_graph && hi - lo == K) {
+            // a full segment: its K adjoint steps read state 0 of the set (the checkpoint's copy) and
+            // states 1 .. K - 1, so they replay one graph per set and starting adjoint buffer,
+            // captured on first use
+            if (!adj_exec[s][a]) {
+                cudaGraph_t g = nullptr;
+                ADJ_CK(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+                cudaError_t e = cudaSuccess;
+                int b = a;
+                for (long r2 = K - 1; r2 >= 0 && e == cudaSuccess; --r2) {
+                    e = lbm::launch_adjoint_step_d2q9(h->prec, arith, sgf_[s][r2], sgg_[s][r2], mu[b],
+                                                      mu[1 - b], h->geo, h->hc, design_face, grad,
+                                                      h->capture_stream);
+                    b = 1 - b;
+                }
+                const cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
+                if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&adj_exec[s][a], g, 0);
+                if (g) cudaGraphDestroy(g);
+                ADJ_CK(e != cudaSuccess ? e : e2);
+            }
+            ADJ_CK(cudaGraphLaunch(adj_exec[s][a], h->stream));
+            if (K & 1) a = 1 - a;
+        } else {
+            for (long k = hi; k >= lo + 1; --k) {
+                ADJ_CK(lbm::launch_adjoint_step_d2q9(h->prec, arith, sf[k - 1 - lo], sg[k - 1 - lo], mu[a],
+                                                     mu[1 - a], h->geo, h->hc, design_face, grad,
+                                                     h->stream));
+                a = 1 - a;
+            }
+        }
+        if (nsets == 2) ADJ_CK(cudaEventRecord(ev_free[s], h->stream));
     }
     ADJ_CK(cudaMemcpyAsync(grad_Tw, grad, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
     ADJ_CK(cudaStreamSynchronize(h->stream));
