@@ -34,6 +34,7 @@ struct HostCoeffs {
     int gopt;   // energy attractors of orders 3-4: 0 = option A, 1 = option B
     int fp16_sr;   // F16S storage: stochastic (1) or nearest (0) rounding of stored deviations
     int index64;   // 1: the step uses 64-bit element offsets even where 32-bit ones suffice
+    int rows3d;    // 3D FP32 / FP16S step: rows of its column each thread updates (1 or 2)
     int adj_sync;  // adjoint step blocks: 0 = 64x2; with phase barriers 1 = 64x4, 2 = 128x2 (default),
                    // 3 = 32x4, 4 = 64x2
 };

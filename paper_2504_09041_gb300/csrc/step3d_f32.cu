@@ -16,7 +16,17 @@ cudaError_t launch_step_d3q27_f32(const void* fin, const void* gin, void* fout, 
     using R = typename S::R;
     const dim3 b = block_shape(geo.nx, block, 3);
     const auto c = make_coeffs<R, 27, 15>(hc);
-    if (step_index32(geo, 27, hc))
+    if (step_index32(geo, 27, hc) && hc.rows3d == 2) {
+        dim3 g = grid_shape(geo, b);
+        g.y = (g.y + 1) / 2;
+        step_d3q27_kernel<S, unsigned, 2><<<g, b, 0, st>>>(
+            (const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo, c, status);
+    } else if (step_index32(geo, 27, hc) && hc.rows3d == 4) {
+        dim3 g = grid_shape(geo, b);
+        g.y = (g.y + 3) / 4;
+        step_d3q27_kernel<S, unsigned, 4><<<g, b, 0, st>>>(
+            (const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo, c, status);
+    } else if (step_index32(geo, 27, hc))
         step_d3q27_kernel<S, unsigned><<<grid_shape(geo, b), b, 0, st>>>(
             (const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo, c, status);
     else

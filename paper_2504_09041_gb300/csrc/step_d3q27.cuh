@@ -576,17 +576,25 @@ struct Launch3D {
     static constexpr int kMinBlocks = sizeof(typename S::R) == 8 ? 1 : 3;
 };
 
-template <class S, class Idx>
+// kRows: each thread updates kRows consecutive rows (y) of its column, one after the other, so a
+// block lives kRows times longer and the SM spends a smaller share of its slots on block
+// turnover.  The grid's y extent is divided by kRows.
+template <class S, class Idx, int kRows = 1>
 __global__ void __launch_bounds__(256, LBM_MINB3D)
     step_d3q27_kernel(const typename S::T* __restrict__ fin, const typename S::T* __restrict__ gin,
                       typename S::T* __restrict__ fout, typename S::T* __restrict__ gout,
                       Geometry geo, Coeffs3D<typename S::R> c, unsigned* status)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * kRows;
     const int z = blockIdx.z;
-    if (x >= geo.nx || y >= geo.ny) return;
-    node_step_d3q27<S, Idx>(fin, gin, fout, gout, geo, c, status, x, y, z);
+    if (x >= geo.nx) return;
+#pragma unroll 1
+    for (int r = 0; r < kRows; ++r) {
+        const int y = y0 + r;
+        if (y >= geo.ny) return;
+        node_step_d3q27<S, Idx>(fin, gin, fout, gout, geo, c, status, x, y, z);
+    }
 }
 
 }  // namespace lbm
