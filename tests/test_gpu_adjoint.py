@@ -133,6 +133,35 @@ def test_adjoint_matches_the_complex_step_oracle(g_option, arith):
         assert grad @ v == pytest.approx(Jc.imag / h, rel=1e-8)
 
 
+@pytest.mark.parametrize("steps,overlap", [(144, 1), (144, 0), (4, 1), (1, 1)])
+def test_adjoint_segment_layouts_match_the_complex_step_oracle(steps, overlap):
+    """The backward pass's bookkeeping for other segment layouts: 144 steps are 12 full segments
+    of an even length (adjoint graphs that keep the buffer parity), with and without the
+    recompute overlapped on the second stream; 4 steps are two segments of 2 (no recompute
+    graph); 1 step has no segment to recompute.  Directional derivative against the generic-form
+    oracle's complex step, 1e-8 relative."""
+    nx, ny, Ra = 22, 18, 1e5
+    bc = O.cavity_bc(2)
+    prof = synth.sine_profile(9, ny)
+    ora = O.Oracle(2, nx, ny, bc=bc, Ra=Ra, Pr=0.71, Ma=0.1)
+    f0, g0 = ora.get_state()
+    lat = L.Lattice("d2q9", nx, ny, Ra=Ra, walls=L.Walls.cavity(2), precision="fp64")
+    lat.set_param("adjoint_overlap", overlap)
+    lat.set_wall_profile(HOT, prof)
+    J, grad = lat.adjoint(steps, COLD, HOT)
+    lat.close()
+    v = np.random.default_rng(23).uniform(-1, 1, ny)
+    h = 1e-20
+    gen = GEN.Generic2D(nx, ny, bc.face, bc.T_wall, bc.T_ref, ora.gbeta, bc.gravity_axis, ora.om_f,
+                        ora.om_g, 0, dtype=np.complex128)
+    gen.set_state(f0, g0)
+    gen.set_wall_profile(HOT, prof + 1j * h * v)
+    gen.step(steps)
+    Jc = gen.nusselt_mean(COLD, ora.L, ora.dT)
+    assert Jc.real == pytest.approx(J, abs=1e-11)
+    assert grad @ v == pytest.approx(Jc.imag / h, rel=1e-8)
+
+
 def test_adjoint_handles_uneven_segments_and_fp32():
     """47 steps (segments of 7, the last one shorter), FP32 states against FP64 states on the same
     problem (default adjoint arithmetic)."""
