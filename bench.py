@@ -184,6 +184,29 @@ def committed_traffic():
     return float(m_t.group(1))
 
 
+def bench_config(w, steps: int, world: int) -> dict:
+    """The `config` of the bench line: the workload, with its sizes.  Both arms (the GPU and the
+    oracle reference) report the same dictionary for the same workload."""
+    three_d = w["lattice"] == "d3q27"
+    n = w["nx"] * w["ny"] * w["nz"]
+    elem = {"fp64": 8, "fp32": 4, "fp16s": 2}[w["precision"]]
+    bpn = 2.0 * ((27 + 15) if three_d else 18) * elem
+    state_gb = bpn / 2 * n / 1e9
+    return {"workload": ("3D differentially heated cubic cavity, D3Q27 flow + D3Q15 energy, "
+                         f"{w['precision'].upper()} populations, FP64 Nusselt reduction")
+            if three_d else
+            ("2D Rayleigh-Benard box, D2Q9 flow + D2Q9 energy, "
+             f"{w['precision'].upper()} populations, FP64 Nusselt reduction"),
+            "nx": w["nx"], "ny": w["ny"], "nz": w["nz"], "Ra": w["Ra"], "Pr": w["Pr"],
+            "Ma": w["Ma"], "nodes_per_gpu": n, "bytes_per_node_update": bpn,
+            "nusselt_every": steps,
+            "l2": (f"inputs larger than L2 ({state_gb:.2f} GB read and {state_gb:.2f} GB "
+                   "written per step)") if state_gb > 0.129 else
+                  f"inputs fit in L2 ({state_gb * 1e3:.0f} MB per step): not an HBM figure",
+            "parallelism": "independent cavity per GPU (ensemble member)" if world > 1
+            else "single GPU"}
+
+
 # ---------------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------------
@@ -285,7 +308,6 @@ def run_gpu(args):
     # the committed ncu traffic describes the 256^3 FP32 step only
     traffic = (committed_traffic() if three_d and w["precision"] == "fp32"
                and (w["nx"], w["ny"], w["nz"]) == (256, 256, 256) else None)
-    state_gb = bpn / 2 * n / 1e9
     e2e = job_mlups(n, args.steps, world, t_e2e)
     line = {
         "metric": METRIC,
@@ -300,19 +322,7 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "fp16s": "f16 storage, f32 arithmetic"}[w["precision"]],
         "data": "synthetic (seeded initial temperature perturbation +-1e-3 of the cavity at rest)",
-        "config": {"workload": ("3D differentially heated cubic cavity, D3Q27 flow + D3Q15 energy, "
-                                f"{w['precision'].upper()} populations, FP64 Nusselt reduction")
-                   if three_d else
-                               ("2D Rayleigh-Benard box, D2Q9 flow + D2Q9 energy, "
-                                f"{w['precision'].upper()} populations, FP64 Nusselt reduction"),
-                   "nx": w["nx"], "ny": w["ny"], "nz": w["nz"], "Ra": w["Ra"], "Pr": w["Pr"],
-                   "Ma": w["Ma"], "nodes_per_gpu": n, "bytes_per_node_update": bpn,
-                   "nusselt_every": args.steps,
-                   "l2": (f"inputs larger than L2 ({state_gb:.2f} GB read and {state_gb:.2f} GB "
-                          "written per step)") if state_gb > 0.129 else
-                         f"inputs fit in L2 ({state_gb * 1e3:.0f} MB per step): not an HBM figure",
-                   "parallelism": "independent cavity per GPU (ensemble member)" if world > 1
-                   else "single GPU"},
+        "config": bench_config(w, args.steps, world),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_kind": peak_kind,
@@ -724,10 +734,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "3D differentially heated cubic cavity, D3Q27 flow + D3Q15 "
-                                   "energy (oracle sample of the 256^3 box)",
-                       "nx": w["nx"], "ny": w["ny"], "nz": w["nz"], "Ra": w["Ra"], "Pr": w["Pr"],
-                       "Ma": w["Ma"]},
+            "config": bench_config(w, args.steps, world),
             "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": O.threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,

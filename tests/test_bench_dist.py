@@ -117,3 +117,13 @@ def test_compact_records_close_the_bench_line():
     assert out["nu_accuracy"][0] == {"case": "2D cavity 64x64, Ra 1e4", "nu_fp64": 2.24,
                                      "fp32_rel": 7.1e-5, "fp16s_rel": 1.1e-3}
     assert len(json.dumps({k: out[k] for k in keys[-2:]})) < 2500
+
+
+def test_reference_arm_reports_the_native_config(capsys):
+    """The oracle arm times the same workload: its config is the native arm's, key for key."""
+    bench.main(["--impl", "reference", "--steps", "1", "--warmup", "3"])
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "MLUPS"
+    assert line["config"] == bench.bench_config(bench.WORKLOAD, 1, 1)
+    assert line["config"]["bytes_per_node_update"] == 336.0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
