@@ -31,8 +31,10 @@
  *       trace (bulk rate) and two deviators (shear rate), by analogy with App. A Step 3; the cascade
  *       runs by order 0-3, 4, 5, 6, each attractor using the post-collision lower moments.
  *   R7  Walls cut half-way between nodes; a link whose source lies beyond a fixed-temperature face
- *       takes anti-bounce-back with that face's temperature (first such face in -x,+x,-y,+y,-z,+z
- *       order), else bounce-back.  Periodic axes wrap first.
+ *       takes anti-bounce-back with that face's temperature, one beyond an adiabatic face
+ *       bounce-back.  A link that crosses two or three walls (box edges and corners) takes the rule
+ *       of the crossed face that comes last in the order -z, -y, -x, +x, +y, +z.  Periodic axes
+ *       wrap first.
  *   R8  Eq. sourceCM2D prints sigma_12 = (F_x/rho) kappa_02 + (F_y/rho) kappa_11; the general
  *       source Eq. forcing:2D (factor n = 2 on the kappa_11 term) and the mirror term of sigma_21
  *       give sigma_12 = (F_x/rho) kappa_02 + 2 (F_y/rho) kappa_11, which is used here.
