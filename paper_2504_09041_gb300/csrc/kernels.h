@@ -169,6 +169,16 @@ inline bool step_index32(const Geometry& g, int q, const HostCoeffs& hc)
     return index32(g, q) && !hc.index64;
 }
 
+// The energy rates are those lbm_create sets (option A; every rate 1 except the first-order ones,
+// which carry alpha), so the 3D step may take the unit-rate energy collision.
+inline bool unit_energy_rates(const HostCoeffs& h)
+{
+    if (h.gopt != 0) return false;
+    for (int b = 4; b < 15; ++b)
+        if (h.om_g[b] != 1.0) return false;
+    return true;
+}
+
 inline dim3 grid_shape(const Geometry& g, dim3 b)
 {
     return dim3((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y, g.nz);

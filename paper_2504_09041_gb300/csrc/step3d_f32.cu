@@ -7,7 +7,10 @@
 
 namespace lbm {
 
-cudaError_t launch_step_d3q27_f32(const void* fin, const void* gin, void* fout, void* gout,
+// kU: the energy rates are those of lbm_create (unit_energy_rates), so the step takes the
+// unit-rate energy collision.
+template <bool kU>
+static cudaError_t launch_plain_f32(const void* fin, const void* gin, void* fout, void* gout,
                                   const Geometry& geo, const HostCoeffs& hc, unsigned* status,
                                   dim3 block, cudaStream_t st)
 {
@@ -19,23 +22,31 @@ cudaError_t launch_step_d3q27_f32(const void* fin, const void* gin, void* fout, 
     if (step_index32(geo, 27, hc) && hc.rows3d == 2) {
         dim3 g = grid_shape(geo, b);
         g.y = (g.y + 1) / 2;
-        step_d3q27_kernel<S, unsigned, 2><<<g, b, 0, st>>>(
+        step_d3q27_kernel<S, unsigned, 2, kU><<<g, b, 0, st>>>(
             (const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo, c, status);
     } else if (step_index32(geo, 27, hc) && hc.rows3d == 4) {
         dim3 g = grid_shape(geo, b);
         g.y = (g.y + 3) / 4;
-        step_d3q27_kernel<S, unsigned, 4><<<g, b, 0, st>>>(
+        step_d3q27_kernel<S, unsigned, 4, kU><<<g, b, 0, st>>>(
             (const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo, c, status);
     } else if (step_index32(geo, 27, hc))
-        step_d3q27_kernel<S, unsigned><<<grid_shape(geo, b), b, 0, st>>>(
+        step_d3q27_kernel<S, unsigned, 1, kU><<<grid_shape(geo, b), b, 0, st>>>(
             (const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo, c, status);
     else
-        step_d3q27_kernel<S, size_t><<<grid_shape(geo, b), b, 0, st>>>(
+        step_d3q27_kernel<S, size_t, 1, kU><<<grid_shape(geo, b), b, 0, st>>>(
             (const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo, c, status);
     return cudaGetLastError();
 }
 
-template <int TY>
+cudaError_t launch_step_d3q27_f32(const void* fin, const void* gin, void* fout, void* gout,
+                                  const Geometry& geo, const HostCoeffs& hc, unsigned* status,
+                                  dim3 block, cudaStream_t st)
+{
+    return unit_energy_rates(hc) ? launch_plain_f32<true>(fin, gin, fout, gout, geo, hc, status, block, st)
+                                 : launch_plain_f32<false>(fin, gin, fout, gout, geo, hc, status, block, st);
+}
+
+template <int TY, bool kU>
 static cudaError_t launch_tma_f32(const TmaMaps& tm, const void* fin, const void* gin, void* fout,
                                   void* gout, const Geometry& geo, const HostCoeffs& hc,
                                   unsigned* status, cudaStream_t st)
@@ -48,7 +59,8 @@ static cudaError_t launch_tma_f32(const TmaMaps& tm, const void* fin, const void
     const int tiles_x = (geo.nx + kTmaTX - 1) / kTmaTX, tiles_y = (geo.ny + TY - 1) / TY;
     const int n_tiles = tiles_x * tiles_y * geo.nz;
     const dim3 block(kTmaTX * TY + 32, 1, 1);   // TY rows of consumers and one producer warp
-    auto kern = step_index32(geo, 27, hc) ? step_d3q27_tma_kernel<S, unsigned, TY> : step_d3q27_tma_kernel<S, size_t, TY>;
+    auto kern = step_index32(geo, 27, hc) ? step_d3q27_tma_kernel<S, unsigned, TY, kU>
+                                          : step_d3q27_tma_kernel<S, size_t, TY, kU>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmemBytes);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
@@ -62,16 +74,25 @@ static cudaError_t launch_tma_f32(const TmaMaps& tm, const void* fin, const void
     return cudaGetLastError();
 }
 
+template <bool kU>
+static cudaError_t launch_tma_rows_f32(const TmaMaps& tm, const void* fin, const void* gin, void* fout,
+                                       void* gout, const Geometry& geo, const HostCoeffs& hc,
+                                       unsigned* status, cudaStream_t st)
+{
+    switch (tm.ty) {
+    case 1: return launch_tma_f32<1, kU>(tm, fin, gin, fout, gout, geo, hc, status, st);
+    case 2: return launch_tma_f32<2, kU>(tm, fin, gin, fout, gout, geo, hc, status, st);
+    case 4: return launch_tma_f32<4, kU>(tm, fin, gin, fout, gout, geo, hc, status, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_step_d3q27_tma_f32(const TmaMaps& tm, const void* fin, const void* gin, void* fout,
                                       void* gout, const Geometry& geo, const HostCoeffs& hc,
                                       unsigned* status, cudaStream_t st)
 {
-    switch (tm.ty) {
-    case 1: return launch_tma_f32<1>(tm, fin, gin, fout, gout, geo, hc, status, st);
-    case 2: return launch_tma_f32<2>(tm, fin, gin, fout, gout, geo, hc, status, st);
-    case 4: return launch_tma_f32<4>(tm, fin, gin, fout, gout, geo, hc, status, st);
-    }
-    return cudaErrorInvalidValue;
+    return unit_energy_rates(hc) ? launch_tma_rows_f32<true>(tm, fin, gin, fout, gout, geo, hc, status, st)
+                                 : launch_tma_rows_f32<false>(tm, fin, gin, fout, gout, geo, hc, status, st);
 }
 
 }  // namespace lbm

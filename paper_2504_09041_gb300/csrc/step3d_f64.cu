@@ -5,9 +5,12 @@
 
 namespace lbm {
 
-cudaError_t launch_step_d3q27_f64(const void* fin, const void* gin, void* fout, void* gout,
-                                  const Geometry& geo, const HostCoeffs& hc, unsigned* status,
-                                  dim3 block, cudaStream_t st)
+// kU: the energy rates are those of lbm_create (unit_energy_rates), so the step takes the
+// unit-rate energy collision.
+template <bool kU>
+static cudaError_t launch_plain_f64(const void* fin, const void* gin, void* fout, void* gout,
+                                    const Geometry& geo, const HostCoeffs& hc, unsigned* status,
+                                    dim3 block, cudaStream_t st)
 {
     using S = StoreF64;
     using T = typename S::T;
@@ -15,12 +18,20 @@ cudaError_t launch_step_d3q27_f64(const void* fin, const void* gin, void* fout, 
     const dim3 b = block_shape(geo.nx, block, 3);
     const auto c = make_coeffs<R, 27, 15>(hc);
     if (step_index32(geo, 27, hc))
-        step_d3q27_kernel<S, unsigned><<<grid_shape(geo, b), b, 0, st>>>(
+        step_d3q27_kernel<S, unsigned, 1, kU><<<grid_shape(geo, b), b, 0, st>>>(
             (const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo, c, status);
     else
-        step_d3q27_kernel<S, size_t><<<grid_shape(geo, b), b, 0, st>>>(
+        step_d3q27_kernel<S, size_t, 1, kU><<<grid_shape(geo, b), b, 0, st>>>(
             (const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo, c, status);
     return cudaGetLastError();
+}
+
+cudaError_t launch_step_d3q27_f64(const void* fin, const void* gin, void* fout, void* gout,
+                                  const Geometry& geo, const HostCoeffs& hc, unsigned* status,
+                                  dim3 block, cudaStream_t st)
+{
+    return unit_energy_rates(hc) ? launch_plain_f64<true>(fin, gin, fout, gout, geo, hc, status, block, st)
+                                 : launch_plain_f64<false>(fin, gin, fout, gout, geo, hc, status, block, st);
 }
 
 }  // namespace lbm

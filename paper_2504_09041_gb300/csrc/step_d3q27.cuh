@@ -439,9 +439,104 @@ __device__ __forceinline__ void collide_g_d3q15(const G15Raw<R>& d, R T_ref, R T
     gd[14] = e * (D0 - D1_);
 }
 
+// D3Q15 energy collision for the rates lbm_create sets (option A; every rate 1 except those of the
+// first-order moments, which carry alpha).  With those rates Step 3 leaves the post-collision
+// central moments as T, the relaxed first-order moments t1 = (1 - omega) eta_1, the second-order
+// c_s^2 T (diagonal) and 0 (mixed), the third-order (2/3) c_s^2 t1 and 0 (111), and
+// eta~_220 = (c_s^2)^2 T: only T and the three first-order raw moments (r100, r010, r001) of the
+// pulled populations enter.  Steps 4-5 are those of collide_g_d3q15 with these values (terms that
+// vanish dropped), so the output is the same up to rounding; it is written to gd as deviations
+// times 2^L.
+template <int L = 0, class R>
+__device__ __forceinline__ void collide_g_d3q15_unit(R T_ref, R T, R r100, R r010, R r001, R ux,
+                                                     R uy, R uz, const R om[15], R gd[15])
+{
+    constexpr double cs2 = 1.0 / 3.0;
+    const R rest2 = R(cs2) * T_ref, rest22 = R(1.0 / 9.0) * T_ref;
+    // Steps 2-3: the first-order central moments, relaxed
+    const R n100 = r100 - ux * T;
+    const R n010 = r010 - uy * T;
+    const R n001 = r001 - uz * T;
+    const R t100 = n100 - om[1] * n100;
+    const R t010 = n010 - om[2] * n010;
+    const R t001 = n001 - om[3] * n001;
+    const R t2 = R(cs2) * T;                       // t200 = t020 = t002
+    const R c3 = R(2.0 / 3.0 * cs2);               // t120 = c3 t100, t012 = c3 t010, t201 = c3 t001
+    const R t220 = R(cs2 * cs2) * T;
+    // Step 4: raw moments (t110 = t101 = t011 = t111 = 0)
+    const R q000 = T;
+    const R q100 = t100 + ux * q000;
+    const R q010 = t010 + uy * q000;
+    const R q001 = t001 + uz * q000;
+    const R q110 = ux * t010 + uy * q100;
+    const R q101 = ux * t001 + uz * q100;
+    const R q011 = uy * t001 + uz * q010;
+    const R q200 = t2 + ux * (t100 + q100);
+    const R q020 = t2 + uy * (t010 + q010);
+    const R q002 = t2 + uz * (t001 + q001);
+    const R q120 = (c3 * t100 + uy * (uy * t100)) + ux * q020;
+    const R q012 = (c3 * t010 + uz * (uz * t010)) + uy * q002;
+    const R q201 = (c3 * t001 + ux * (ux * t001)) + uz * q200;
+    const R q111 = uy * (ux * t001) + uz * q110;
+    const R Z1 = q012 - ux * (R(2) * q110 - ux * q010);
+    const R Z2 = t220 + uy * (R(2) * Z1 - uy * t2);
+    const R q220 = Z2 + ux * (R(2) * q120 - ux * q020);
+    // Step 5: populations of the deviations
+    const R q000d = q000 - T_ref, q200d = q200 - rest2, q020d = q020 - rest2, q002d = q002 - rest2;
+    const R q220d = q220 - rest22;
+    const R Sx = q200d - q220d, Dx = q100 - q120;
+    const R Sy = q020d - q220d, Dy = q010 - q012;
+    const R Sz = q002d - q220d, Dz = q001 - q201;
+    constexpr double s = double(1ull << L);
+    const R g0 = q000d - q200d - q020d - q002d + R(2) * q220d;
+    gd[0] = L == 0 ? g0 : R(s) * g0;
+    const R hs = R(0.5 * s);
+    gd[1] = hs * (Sx + Dx);
+    gd[2] = hs * (Sx - Dx);
+    gd[3] = hs * (Sy + Dy);
+    gd[4] = hs * (Sy - Dy);
+    gd[5] = hs * (Sz + Dz);
+    gd[6] = hs * (Sz - Dz);
+    const R e = R(0.125 * s);
+    const R P_s = q220d + q201, M_s = q220d - q201;
+    const R P_y = q012 + q011, M_y = q012 - q011;
+    const R P_x = q120 + q101, M_x = q120 - q101;
+    const R P_xy = q110 + q111, M_xy = q110 - q111;
+    const R A0 = P_s + P_y, B0 = P_s - P_y, A1 = P_x + P_xy, B1 = P_x - P_xy;
+    const R C0 = M_s + M_y, D0 = M_s - M_y, C1_ = M_x + M_xy, D1_ = M_x - M_xy;
+    gd[7] = e * (A0 + A1);
+    gd[8] = e * (A0 - A1);
+    gd[9] = e * (B0 + B1);
+    gd[10] = e * (B0 - B1);
+    gd[11] = e * (C0 + C1_);
+    gd[12] = e * (C0 - C1_);
+    gd[13] = e * (D0 + D1_);
+    gd[14] = e * (D0 - D1_);
+}
+
+// Zeroth and first raw moments of the D3Q15 deviations (the part of raw_g_d3q15 that the
+// unit-rate energy collision needs).
+template <class R>
+__device__ __forceinline__ void raw01_g_d3q15(const R g[15], R& r000, R& r100, R& r010, R& r001)
+{
+    const R a0 = g[7] + g[8], a1 = g[7] - g[8];     // y+ z+
+    const R b0 = g[9] + g[10], b1 = g[9] - g[10];   // y- z+
+    const R c0 = g[11] + g[12], c1 = g[11] - g[12]; // y+ z-
+    const R d0 = g[13] + g[14], d1 = g[13] - g[14]; // y- z-
+    const R zp_s = a0 + b0, zm_s = c0 + d0;
+    const R C1 = zp_s + zm_s, Cz = zp_s - zm_s;
+    const R Cy = (a0 - b0) + (c0 - d0);
+    const R Cx = (a1 + b1) + (c1 + d1);
+    r000 = g[0] + (g[1] + g[2]) + (g[3] + g[4]) + (g[5] + g[6]) + C1;
+    r100 = (g[1] - g[2]) + Cx;
+    r010 = (g[3] - g[4]) + Cy;
+    r001 = (g[5] - g[6]) + Cz;
+}
+
 // Macroscopic fields, both collisions and the store of one node whose pulled deviations are in
-// f (flow) and g (energy); i is the node's linear index.
-template <class S, class Idx>
+// f (flow) and g (energy); i is the node's linear index.  kUnitG: the energy rates are those of
+// lbm_create (see collide_g_d3q15_unit), which the host has checked.
+template <class S, class Idx, bool kUnitG = false>
 __device__ __forceinline__ void collide_store_d3q27(typename S::R f[27], typename S::R g[15],
                                                     typename S::T* __restrict__ fout,
                                                     typename S::T* __restrict__ gout,
@@ -449,7 +544,7 @@ __device__ __forceinline__ void collide_store_d3q27(typename S::R f[27], typenam
                                                     const Coeffs3D<typename S::R>& c,
                                                     unsigned* status, int i);
 
-template <class S, class Idx>
+template <class S, class Idx, bool kUnitG = false>
 __device__ __forceinline__ void node_step_d3q27(const typename S::T* __restrict__ fin,
                                                 const typename S::T* __restrict__ gin,
                                                 typename S::T* __restrict__ fout,
@@ -476,10 +571,10 @@ __device__ __forceinline__ void node_step_d3q27(const typename S::T* __restrict_
         const NodeWalls<R> w = node_walls<R>(geo, x, y, z, 3);
         pull_d3q27_d3q15<S, Idx>(fin, gin, geo, w, i, c.T_ref, f, g);
     }
-    collide_store_d3q27<S, Idx>(f, g, fout, gout, geo, c, status, i);
+    collide_store_d3q27<S, Idx, kUnitG>(f, g, fout, gout, geo, c, status, i);
 }
 
-template <class S, class Idx>
+template <class S, class Idx, bool kUnitG>
 __device__ __forceinline__ void collide_store_d3q27(typename S::R f[27], typename S::R g[15],
                                                     typename S::T* __restrict__ fout,
                                                     typename S::T* __restrict__ gout,
@@ -490,8 +585,13 @@ __device__ __forceinline__ void collide_store_d3q27(typename S::R f[27], typenam
     using R = typename S::R;
     // rho = 1 + sum delta, rho u = sum delta e + F/2, T = T_o + sum gamma (the zeroth raw moment of
     // the energy deviations, which the energy collision starts from)
-    const G15Raw<R> gr = raw_g_d3q15(g);
-    const R dT = gr.r000;
+    G15Raw<R> gr;
+    R dT;
+    if constexpr (kUnitG) raw01_g_d3q15(g, dT, gr.r100, gr.r010, gr.r001);
+    else {
+        gr = raw_g_d3q15(g);
+        dT = gr.r000;
+    }
     // Density and momentum: from the raw x-line values for FP16 and FP64 storage, which are bound by
     // the instruction or FP64 rate (51 fewer additions; FP16S +1.2 %); directly from the links for
     // FP32 storage, where keeping the nine line values live adds spills (-0.6 % measured).
@@ -544,7 +644,8 @@ __device__ __forceinline__ void collide_store_d3q27(typename S::R f[27], typenam
     constexpr int kL = kF16 ? StoreF16S::kScaleLog2 : 0;
     from_central_d3q27<kL>(p, f, ux, uy, uz);
     // energy collision on the deviations: g receives the post-collision gamma
-    collide_g_d3q15<kL>(gr, c.T_ref, T, ux, uy, uz, c.om_g, c.gopt, g);
+    if constexpr (kUnitG) collide_g_d3q15_unit<kL>(c.T_ref, T, gr.r100, gr.r010, gr.r001, ux, uy, uz, c.om_g, g);
+    else collide_g_d3q15<kL>(gr, c.T_ref, T, ux, uy, uz, c.om_g, c.gopt, g);
 
     if constexpr (kF16) {
         if (c.fp16_sr) {
@@ -579,7 +680,7 @@ struct Launch3D {
 // kRows: each thread updates kRows consecutive rows (y) of its column, one after the other, so a
 // block lives kRows times longer and the SM spends a smaller share of its slots on block
 // turnover.  The grid's y extent is divided by kRows.
-template <class S, class Idx, int kRows = 1>
+template <class S, class Idx, int kRows = 1, bool kUnitG = false>
 __global__ void __launch_bounds__(256, LBM_MINB3D)
     step_d3q27_kernel(const typename S::T* __restrict__ fin, const typename S::T* __restrict__ gin,
                       typename S::T* __restrict__ fout, typename S::T* __restrict__ gout,
@@ -593,7 +694,7 @@ __global__ void __launch_bounds__(256, LBM_MINB3D)
     for (int r = 0; r < kRows; ++r) {
         const int y = y0 + r;
         if (y >= geo.ny) return;
-        node_step_d3q27<S, Idx>(fin, gin, fout, gout, geo, c, status, x, y, z);
+        node_step_d3q27<S, Idx, kUnitG>(fin, gin, fout, gout, geo, c, status, x, y, z);
     }
 }
 

@@ -186,6 +186,31 @@ def test_fp64_step_parity_3d(kind, shape):
     assert pop_error(gpu, ora) <= 1e-12
 
 
+@pytest.mark.parametrize("kind,shape", PARITY_3D)
+@pytest.mark.parametrize("random_flow_rates", [False, True])
+def test_fp64_step_parity_3d_unit_energy_rates(kind, shape, random_flow_rates):
+    """With the energy rates of lbm_create (every rate 1 except the first-order ones) the 3D step
+    takes the reduced energy collision (only T and the first-order moments enter).  Against the
+    oracle, which runs App. C's full Steps 1-5: the same bars as the general step, with the
+    default rates and with random flow rates and first-order energy rates."""
+    nz, ny, nx = shape
+    gpu, ora = make_pair(3, nx, ny, nz, kind=kind)
+    om_f, om_g = ora.om_f.copy(), ora.om_g.copy()
+    assert np.all(om_g[4:] == 1.0)
+    if random_flow_rates:
+        om_f = synth.rates(31, 27, 0.7, 1.7)
+        om_g[1:4] = synth.rates(32, 3, 0.7, 1.7)
+    ora = O.Oracle(3, nx, ny, nz, bc=walls_pair(kind, 3)[1], om_f=om_f, om_g=om_g, gbeta=3e-3)
+    gpu.set_omegas(om_f, om_g)
+    gpu.set_param("gbeta", 3e-3)
+    randomize(gpu, ora, 16, scale=0.05)
+    gpu.step(1); ora.step(1)
+    assert pop_error(gpu, ora) <= 1e-14
+    gpu.step(99); ora.step(99)
+    gpu.sync()
+    assert pop_error(gpu, ora) <= 1e-12
+
+
 @pytest.mark.parametrize("dim,shape", [(2, (1, 37, 131)), (3, (13, 21, 37))])
 def test_fp64_step_parity_option_b(dim, shape):
     """The renormalized option-B energy attractors (Eq. MvT2DoptionB, Sec. 5.3 D3Q15 list), with
