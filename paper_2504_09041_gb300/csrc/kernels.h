@@ -179,6 +179,23 @@ inline bool unit_energy_rates(const HostCoeffs& h)
     return true;
 }
 
+// The 3D flow rates are those lbm_create sets: every rate 1 except the shear rates (slots 4-6,
+// 8, 9), the bulk rate (slot 7) included.
+inline bool unit_flow_rates(const HostCoeffs& h)
+{
+    for (int a = 0; a < 27; ++a)
+        if (!(a >= 4 && a <= 6) && a != 8 && a != 9 && h.om_f[a] != 1.0) return false;
+    return true;
+}
+
+// Which collision instance the 3D step takes: 0 general, 1 unit-rate energy collision, 2 that and
+// the unit-rate flow relaxation.
+inline int rate_class(const HostCoeffs& h)
+{
+    if (!unit_energy_rates(h)) return 0;
+    return unit_flow_rates(h) ? 2 : 1;
+}
+
 inline dim3 grid_shape(const Geometry& g, dim3 b)
 {
     return dim3((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y, g.nz);

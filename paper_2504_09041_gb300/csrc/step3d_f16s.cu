@@ -7,9 +7,9 @@
 
 namespace lbm {
 
-// kU: the energy rates are those of lbm_create (unit_energy_rates), so the step takes the
-// unit-rate energy collision.
-template <bool kU>
+// kU: the collision instance for the rates (rate_class: 0 general, 1 unit-rate energy collision,
+// 2 unit-rate energy collision and flow relaxation).
+template <int kU>
 static cudaError_t launch_plain_f16s(const void* fin, const void* gin, void* fout, void* gout,
                                   const Geometry& geo, const HostCoeffs& hc, unsigned* status,
                                   dim3 block, cudaStream_t st)
@@ -42,11 +42,14 @@ cudaError_t launch_step_d3q27_f16s(const void* fin, const void* gin, void* fout,
                                   const Geometry& geo, const HostCoeffs& hc, unsigned* status,
                                   dim3 block, cudaStream_t st)
 {
-    return unit_energy_rates(hc) ? launch_plain_f16s<true>(fin, gin, fout, gout, geo, hc, status, block, st)
-                                 : launch_plain_f16s<false>(fin, gin, fout, gout, geo, hc, status, block, st);
+    switch (rate_class(hc)) {
+    case 2: return launch_plain_f16s<2>(fin, gin, fout, gout, geo, hc, status, block, st);
+    case 1: return launch_plain_f16s<1>(fin, gin, fout, gout, geo, hc, status, block, st);
+    }
+    return launch_plain_f16s<0>(fin, gin, fout, gout, geo, hc, status, block, st);
 }
 
-template <int TY, bool kU>
+template <int TY, int kU>
 static cudaError_t launch_tma_f16s(const TmaMaps& tm, const void* fin, const void* gin, void* fout,
                                   void* gout, const Geometry& geo, const HostCoeffs& hc,
                                   unsigned* status, cudaStream_t st)
@@ -74,7 +77,7 @@ static cudaError_t launch_tma_f16s(const TmaMaps& tm, const void* fin, const voi
     return cudaGetLastError();
 }
 
-template <bool kU>
+template <int kU>
 static cudaError_t launch_tma_rows_f16s(const TmaMaps& tm, const void* fin, const void* gin, void* fout,
                                        void* gout, const Geometry& geo, const HostCoeffs& hc,
                                        unsigned* status, cudaStream_t st)
@@ -91,8 +94,11 @@ cudaError_t launch_step_d3q27_tma_f16s(const TmaMaps& tm, const void* fin, const
                                       void* gout, const Geometry& geo, const HostCoeffs& hc,
                                       unsigned* status, cudaStream_t st)
 {
-    return unit_energy_rates(hc) ? launch_tma_rows_f16s<true>(tm, fin, gin, fout, gout, geo, hc, status, st)
-                                 : launch_tma_rows_f16s<false>(tm, fin, gin, fout, gout, geo, hc, status, st);
+    switch (rate_class(hc)) {
+    case 2: return launch_tma_rows_f16s<2>(tm, fin, gin, fout, gout, geo, hc, status, st);
+    case 1: return launch_tma_rows_f16s<1>(tm, fin, gin, fout, gout, geo, hc, status, st);
+    }
+    return launch_tma_rows_f16s<0>(tm, fin, gin, fout, gout, geo, hc, status, st);
 }
 
 }  // namespace lbm

@@ -5,9 +5,9 @@
 
 namespace lbm {
 
-// kU: the energy rates are those of lbm_create (unit_energy_rates), so the step takes the
-// unit-rate energy collision.
-template <bool kU>
+// kU: the collision instance for the rates (rate_class: 0 general, 1 unit-rate energy collision,
+// 2 unit-rate energy collision and flow relaxation).
+template <int kU>
 static cudaError_t launch_plain_f64(const void* fin, const void* gin, void* fout, void* gout,
                                     const Geometry& geo, const HostCoeffs& hc, unsigned* status,
                                     dim3 block, cudaStream_t st)
@@ -30,8 +30,11 @@ cudaError_t launch_step_d3q27_f64(const void* fin, const void* gin, void* fout, 
                                   const Geometry& geo, const HostCoeffs& hc, unsigned* status,
                                   dim3 block, cudaStream_t st)
 {
-    return unit_energy_rates(hc) ? launch_plain_f64<true>(fin, gin, fout, gout, geo, hc, status, block, st)
-                                 : launch_plain_f64<false>(fin, gin, fout, gout, geo, hc, status, block, st);
+    switch (rate_class(hc)) {
+    case 2: return launch_plain_f64<2>(fin, gin, fout, gout, geo, hc, status, block, st);
+    case 1: return launch_plain_f64<1>(fin, gin, fout, gout, geo, hc, status, block, st);
+    }
+    return launch_plain_f64<0>(fin, gin, fout, gout, geo, hc, status, block, st);
 }
 
 }  // namespace lbm

@@ -82,10 +82,15 @@ __device__ __forceinline__ void pull_d3q27_d3q15_interior(const typename S::T* _
 // on entry, kappa~_abc - K_abc on exit.  Rate slots follow the moment order of Sec. 5.2; slot 7
 // relaxes the trace (bulk), slots 8 and 9 the deviators kappa_200 - kappa_020, kappa_200 - kappa_002.
 // Sources (Eq. forcing:3D) use the full pre-collision moments kappa = K + D.
-template <class R>
+// kUnit: the rates are those of lbm_create (every rate 1 except the shear ones, slots 4-6, 8, 9;
+// unit_flow_rates), which the host has checked.  A moment relaxed at rate 1 lands on its attractor
+// plus half its source, so its pre-collision value drops out of its own update (order 6 drops out
+// entirely).
+template <bool kUnit = false, class R>
 __device__ __forceinline__ void relax_f_d3q27(R D[3][3][3], R drho, R irho, R ux, R uy, R uz, R Fx,
                                               R Fy, R Fz, const Coeffs3D<R>& c)
 {
+    const R hu = R(0.5);   // 1 - omega / 2 at omega = 1
 #define DD(a, b, cc) D[cc][b][a]
     const R* om = c.om_f;
     const R* h = c.hf;
@@ -117,10 +122,10 @@ __device__ __forceinline__ void relax_f_d3q27(R D[3][3][3], R drho, R irho, R ux
     const R k122 = d122 - ux * B * C, k212 = d212 - A * uy * C, k221 = d221 - A * B * uz;
 
     // orders 0 and 1 (K_000 = 1, K_100 = -ux, ...)
-    const R t000 = d000 + om[0] * (drho - d000);
-    const R t100 = d100 - om[1] * (d100 - ux) + h[1] * Fx;
-    const R t010 = d010 - om[2] * (d010 - uy) + h[2] * Fy;
-    const R t001 = d001 - om[3] * (d001 - uz) + h[3] * Fz;
+    const R t000 = kUnit ? drho : d000 + om[0] * (drho - d000);
+    const R t100 = kUnit ? ux + hu * Fx : d100 - om[1] * (d100 - ux) + h[1] * Fx;
+    const R t010 = kUnit ? uy + hu * Fy : d010 - om[2] * (d010 - uy) + h[2] * Fy;
+    const R t001 = kUnit ? uz + hu * Fz : d001 - om[3] * (d001 - uz) + h[3] * Fz;
 
     // order 2: off-diagonal toward 0, trace toward rho, deviators toward 0
     const R t110 = d110 - om[4] * (d110 + xy);
@@ -128,21 +133,26 @@ __device__ __forceinline__ void relax_f_d3q27(R D[3][3][3], R drho, R irho, R ux
     const R t011 = d011 - om[6] * (d011 + yz);
     const R dtr = d200 + d020 + d002;
     const R dd1 = d200 - d020, dd2 = d200 - d002;
-    const R ttr = dtr + om[7] * (drho - (ux * ux + uy * uy + uz * uz) - dtr);
+    const R ttr = kUnit ? drho - (ux * ux + uy * uy + uz * uz)
+                        : dtr + om[7] * (drho - (ux * ux + uy * uy + uz * uz) - dtr);
     const R td1 = dd1 - om[8] * (dd1 + ux * ux - uy * uy);
     const R td2 = dd2 - om[9] * (dd2 + ux * ux - uz * uz);
     const R t200 = third * (ttr + td1 + td2);
     const R t020 = third * (ttr - R(2) * td1 + td2);
     const R t002 = third * (ttr + td1 - R(2) * td2);
 
-    // order 3: attractors zero
-    const R t120 = d120 - om[10] * k120 + h[10] * (Fxr * k020 + R(2) * Fyr * k110);
-    const R t102 = d102 - om[11] * k102 + h[11] * (Fxr * k002 + R(2) * Fzr * k101);
-    const R t210 = d210 - om[12] * k210 + h[12] * (R(2) * Fxr * k110 + Fyr * k200);
-    const R t012 = d012 - om[13] * k012 + h[13] * (Fyr * k002 + R(2) * Fzr * k011);
-    const R t201 = d201 - om[14] * k201 + h[14] * (R(2) * Fxr * k101 + Fzr * k200);
-    const R t021 = d021 - om[15] * k021 + h[15] * (R(2) * Fyr * k011 + Fzr * k020);
-    const R t111 = d111 - om[16] * k111 + h[16] * (Fxr * k011 + Fyr * k101 + Fzr * k110);
+    // order 3: attractors zero (at rate 1 the deviation is -K plus half the source)
+    const R s120 = Fxr * k020 + R(2) * Fyr * k110, s102 = Fxr * k002 + R(2) * Fzr * k101;
+    const R s210 = R(2) * Fxr * k110 + Fyr * k200, s012 = Fyr * k002 + R(2) * Fzr * k011;
+    const R s201 = R(2) * Fxr * k101 + Fzr * k200, s021 = R(2) * Fyr * k011 + Fzr * k020;
+    const R s111 = Fxr * k011 + Fyr * k101 + Fzr * k110;
+    const R t120 = kUnit ? ux * B + hu * s120 : d120 - om[10] * k120 + h[10] * s120;
+    const R t102 = kUnit ? ux * C + hu * s102 : d102 - om[11] * k102 + h[11] * s102;
+    const R t210 = kUnit ? A * uy + hu * s210 : d210 - om[12] * k210 + h[12] * s210;
+    const R t012 = kUnit ? uy * C + hu * s012 : d012 - om[13] * k012 + h[13] * s012;
+    const R t201 = kUnit ? A * uz + hu * s201 : d201 - om[14] * k201 + h[14] * s201;
+    const R t021 = kUnit ? B * uz + hu * s021 : d021 - om[15] * k021 + h[15] * s021;
+    const R t111 = kUnit ? xy * uz + hu * s111 : d111 - om[16] * k111 + h[16] * s111;
 
     // full post-collision moments of orders 2-3 (small, or O(1) only through A, B, C)
     const R p110 = xy + t110, p101 = xz + t101, p011 = yz + t011;
@@ -157,12 +167,17 @@ __device__ __forceinline__ void relax_f_d3q27(R D[3][3][3], R drho, R irho, R ux
     const R M211 = ((A + t200) * p011 + R(2) * p110 * p101) * irho - A * yz;
     const R M121 = ((B + t020) * p101 + R(2) * p110 * p011) * irho - B * xz;
     const R M112 = ((C + t002) * p110 + R(2) * p011 * p101) * irho - C * xy;
-    const R t220 = d220 + om[17] * (M220 - d220) + h[17] * R(2) * (Fxr * k120 + Fyr * k210);
-    const R t202 = d202 + om[18] * (M202 - d202) + h[18] * R(2) * (Fxr * k102 + Fzr * k201);
-    const R t022 = d022 + om[19] * (M022 - d022) + h[19] * R(2) * (Fyr * k012 + Fzr * k021);
-    const R t211 = d211 + om[20] * (M211 - d211) + h[20] * (R(2) * Fxr * k111 + Fyr * k201 + Fzr * k210);
-    const R t121 = d121 + om[21] * (M121 - d121) + h[21] * (Fxr * k021 + R(2) * Fyr * k111 + Fzr * k120);
-    const R t112 = d112 + om[22] * (M112 - d112) + h[22] * (Fxr * k012 + Fyr * k102 + R(2) * Fzr * k111);
+    const R s220 = R(2) * (Fxr * k120 + Fyr * k210), s202 = R(2) * (Fxr * k102 + Fzr * k201);
+    const R s022 = R(2) * (Fyr * k012 + Fzr * k021);
+    const R s211 = R(2) * Fxr * k111 + Fyr * k201 + Fzr * k210;
+    const R s121 = Fxr * k021 + R(2) * Fyr * k111 + Fzr * k120;
+    const R s112 = Fxr * k012 + Fyr * k102 + R(2) * Fzr * k111;
+    const R t220 = kUnit ? M220 + hu * s220 : d220 + om[17] * (M220 - d220) + h[17] * s220;
+    const R t202 = kUnit ? M202 + hu * s202 : d202 + om[18] * (M202 - d202) + h[18] * s202;
+    const R t022 = kUnit ? M022 + hu * s022 : d022 + om[19] * (M022 - d022) + h[19] * s022;
+    const R t211 = kUnit ? M211 + hu * s211 : d211 + om[20] * (M211 - d211) + h[20] * s211;
+    const R t121 = kUnit ? M121 + hu * s121 : d121 + om[21] * (M121 - d121) + h[21] * s121;
+    const R t112 = kUnit ? M112 + hu * s112 : d112 + om[22] * (M112 - d112) + h[22] * s112;
 
     // order 5: attractors from post-collision orders 2 and 3 (K_122 = -ux B C, ...)
     const R f25 = R(2.0 / 5.0) * irho;
@@ -173,9 +188,12 @@ __device__ __forceinline__ void relax_f_d3q27(R D[3][3][3], R drho, R irho, R ux
                           + R(2) * (p110 * p102 + p011 * p201)) + A * uy * C;
     const R M221 = f25 * (q200 * p021 + q020 * p201 + R(4) * p110 * p111
                           + R(2) * (p011 * p210 + p101 * p120)) + A * B * uz;
-    const R t122 = d122 + om[23] * (M122 - d122) + h[23] * (Fxr * k022 + R(2) * (Fyr * k112 + Fzr * k121));
-    const R t212 = d212 + om[24] * (M212 - d212) + h[24] * (Fyr * k202 + R(2) * (Fxr * k112 + Fzr * k211));
-    const R t221 = d221 + om[25] * (M221 - d221) + h[25] * (Fzr * k220 + R(2) * (Fxr * k121 + Fyr * k211));
+    const R s122 = Fxr * k022 + R(2) * (Fyr * k112 + Fzr * k121);
+    const R s212 = Fyr * k202 + R(2) * (Fxr * k112 + Fzr * k211);
+    const R s221 = Fzr * k220 + R(2) * (Fxr * k121 + Fyr * k211);
+    const R t122 = kUnit ? M122 + hu * s122 : d122 + om[23] * (M122 - d122) + h[23] * s122;
+    const R t212 = kUnit ? M212 + hu * s212 : d212 + om[24] * (M212 - d212) + h[24] * s212;
+    const R t221 = kUnit ? M221 + hu * s221 : d221 + om[25] * (M221 - d221) + h[25] * s221;
 
     // order 6: attractor from post-collision orders 2 and 4, K_222 = A B C
     const R p112 = C * xy + t112, p121 = B * xz + t121, p211 = A * yz + t211;
@@ -183,7 +201,8 @@ __device__ __forceinline__ void relax_f_d3q27(R D[3][3][3], R drho, R irho, R ux
                  * (A * t022 + B * t202 + C * t220 + B * C * t200 + A * C * t020 + A * B * t002
                     + t200 * t022 + t020 * t202 + t002 * t220
                     + R(4) * (p110 * p112 + p101 * p121 + p011 * p211) - R(3) * A * B * C * drho);
-    const R t222 = d222 + om[26] * (M222 - d222) + h[26] * R(2) * (Fxr * k122 + Fyr * k212 + Fzr * k221);
+    const R s222 = R(2) * (Fxr * k122 + Fyr * k212 + Fzr * k221);
+    const R t222 = kUnit ? M222 + hu * s222 : d222 + om[26] * (M222 - d222) + h[26] * s222;
 
     DD(0, 0, 0) = t000; DD(1, 0, 0) = t100; DD(0, 1, 0) = t010; DD(0, 0, 1) = t001;
     DD(1, 1, 0) = t110; DD(1, 0, 1) = t101; DD(0, 1, 1) = t011;
@@ -534,9 +553,10 @@ __device__ __forceinline__ void raw01_g_d3q15(const R g[15], R& r000, R& r100, R
 }
 
 // Macroscopic fields, both collisions and the store of one node whose pulled deviations are in
-// f (flow) and g (energy); i is the node's linear index.  kUnitG: the energy rates are those of
-// lbm_create (see collide_g_d3q15_unit), which the host has checked.
-template <class S, class Idx, bool kUnitG = false>
+// f (flow) and g (energy); i is the node's linear index.  kRates (rate_class, checked by the host):
+// 0 general rates; 1 the energy rates of lbm_create (collide_g_d3q15_unit); 2 the flow rates of
+// lbm_create as well (relax_f_d3q27<true>).
+template <class S, class Idx, int kRates = 0>
 __device__ __forceinline__ void collide_store_d3q27(typename S::R f[27], typename S::R g[15],
                                                     typename S::T* __restrict__ fout,
                                                     typename S::T* __restrict__ gout,
@@ -544,7 +564,7 @@ __device__ __forceinline__ void collide_store_d3q27(typename S::R f[27], typenam
                                                     const Coeffs3D<typename S::R>& c,
                                                     unsigned* status, int i);
 
-template <class S, class Idx, bool kUnitG = false>
+template <class S, class Idx, int kRates = 0>
 __device__ __forceinline__ void node_step_d3q27(const typename S::T* __restrict__ fin,
                                                 const typename S::T* __restrict__ gin,
                                                 typename S::T* __restrict__ fout,
@@ -571,10 +591,10 @@ __device__ __forceinline__ void node_step_d3q27(const typename S::T* __restrict_
         const NodeWalls<R> w = node_walls<R>(geo, x, y, z, 3);
         pull_d3q27_d3q15<S, Idx>(fin, gin, geo, w, i, c.T_ref, f, g);
     }
-    collide_store_d3q27<S, Idx, kUnitG>(f, g, fout, gout, geo, c, status, i);
+    collide_store_d3q27<S, Idx, kRates>(f, g, fout, gout, geo, c, status, i);
 }
 
-template <class S, class Idx, bool kUnitG>
+template <class S, class Idx, int kRates>
 __device__ __forceinline__ void collide_store_d3q27(typename S::R f[27], typename S::R g[15],
                                                     typename S::T* __restrict__ fout,
                                                     typename S::T* __restrict__ gout,
@@ -585,6 +605,7 @@ __device__ __forceinline__ void collide_store_d3q27(typename S::R f[27], typenam
     using R = typename S::R;
     // rho = 1 + sum delta, rho u = sum delta e + F/2, T = T_o + sum gamma (the zeroth raw moment of
     // the energy deviations, which the energy collision starts from)
+    constexpr bool kUnitG = kRates >= 1, kUnitF = kRates >= 2;
     G15Raw<R> gr;
     R dT;
     if constexpr (kUnitG) raw01_g_d3q15(g, dT, gr.r100, gr.r010, gr.r001);
@@ -638,7 +659,7 @@ __device__ __forceinline__ void collide_store_d3q27(typename S::R f[27], typenam
 
     if constexpr (!kLineSums) xraw_d3q27(f, p);
     central_from_xraw_d3q27(p, ux, uy, uz);
-    relax_f_d3q27(p, drho, irho, ux, uy, uz, Fx, Fy, Fz, c);
+    relax_f_d3q27<kUnitF>(p, drho, irho, ux, uy, uz, Fx, Fy, Fz, c);
     // FP16 storage keeps deviations times 2^10: both collisions return them already scaled
     constexpr bool kF16 = std::is_same<S, StoreF16S>::value;
     constexpr int kL = kF16 ? StoreF16S::kScaleLog2 : 0;
@@ -680,7 +701,7 @@ struct Launch3D {
 // kRows: each thread updates kRows consecutive rows (y) of its column, one after the other, so a
 // block lives kRows times longer and the SM spends a smaller share of its slots on block
 // turnover.  The grid's y extent is divided by kRows.
-template <class S, class Idx, int kRows = 1, bool kUnitG = false>
+template <class S, class Idx, int kRows = 1, int kRates = 0>
 __global__ void __launch_bounds__(256, LBM_MINB3D)
     step_d3q27_kernel(const typename S::T* __restrict__ fin, const typename S::T* __restrict__ gin,
                       typename S::T* __restrict__ fout, typename S::T* __restrict__ gout,
@@ -694,7 +715,7 @@ __global__ void __launch_bounds__(256, LBM_MINB3D)
     for (int r = 0; r < kRows; ++r) {
         const int y = y0 + r;
         if (y >= geo.ny) return;
-        node_step_d3q27<S, Idx, kUnitG>(fin, gin, fout, gout, geo, c, status, x, y, z);
+        node_step_d3q27<S, Idx, kRates>(fin, gin, fout, gout, geo, c, status, x, y, z);
     }
 }
 

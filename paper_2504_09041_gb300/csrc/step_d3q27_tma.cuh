@@ -176,7 +176,7 @@ __device__ __forceinline__ void fix_x_edge_d3q27(const typename S::T* __restrict
 // fastest, then y, then z), walked with incrementally updated coordinates.  Stage s of the
 // kStages-deep ring has a "full" barrier (the copies of its tile have landed) and an "empty"
 // barrier (every consumer warp is done with it); no block-wide barrier is used in the loop.
-template <class S, class Idx, int TY, bool kUnitG = false>
+template <class S, class Idx, int TY, int kRates = 0>
 __global__ void __launch_bounds__(kTmaTX * TY + 32, TmaLayout<typename S::T, TY>::kMinBlocks)
     step_d3q27_tma_kernel(const __grid_constant__ CUtensorMap mf, const __grid_constant__ CUtensorMap mg,
                           const typename S::T* __restrict__ fin, const typename S::T* __restrict__ gin,
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(kTmaTX * TY + 32, TmaLayout<typename S::T, TY>
                     const NodeWalls<R> w = node_walls<R>(geo, x, y, z, 3);
                     pull_d3q27_d3q15<S, Idx>(fin, gin, geo, w, i, c.T_ref, f, g);
                 }
-                collide_store_d3q27<S, Idx, kUnitG>(f, g, fout, gout, geo, c, status, i);
+                collide_store_d3q27<S, Idx, kRates>(f, g, fout, gout, geo, c, status, i);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(empty_bar(st));   // this warp is done with stage st
