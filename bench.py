@@ -406,10 +406,11 @@ def compact_nu_accuracy(nu_acc):
              "fp16s_rel": float(f"{a['rel_vs_fp64']['fp16s']:.3g}")} for a in nu_acc]
 
 
-# FP64 lane operations per node update of the FP64 steps (ncu instruction counts of the FP64
-# kernels, committed with the profiles) and GB300's FP64 pipe rate: 2 lane operations per SM per
+# FP64 lane operations per node update of the FP64 steps at the default rates (ncu instruction
+# counts of the FP64 kernels, committed with the profiles; the 3D count is that of the reduced
+# collisions the default rates select) and GB300's FP64 pipe rate: 2 lane operations per SM per
 # clock.
-FP64_OPS_PER_NODE = {"d3q27": 973.8, "d2q9": 340.6}
+FP64_OPS_PER_NODE = {"d3q27": 866.8, "d2q9": 340.6}
 FP64_LANE_OPS_PER_SM_CLK = 2
 
 

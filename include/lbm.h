@@ -146,7 +146,8 @@ LBM_API int lbm_set_omegas(lbm_handle h, const double* om_f, int n_f, const doub
  * a second set of segment buffers; 0: one stream, one set),
  * "graph_steps" (even count of steps that lbm_step replays as one CUDA graph; 0 disables),
  * "rows3d" (1, 2 or 4: rows of its column that each thread of the 3D FP32 / FP16S step updates
- * in turn; results are bitwise the same),
+ * in turn; 0, the default: the faster count measured for the storage and rates, one for FP16S
+ * with the default rates and two otherwise; results are bitwise the same),
  * "index64" (1: the step kernels use 64-bit element offsets, the instantiation that boxes with
  * q n >= 2^32 run, on any box; results are bitwise those of the 32-bit form; for testing that path), or the
  * thread-block shape of the step launch, "block_x" (32, 64, 128 or 256) and "block_y"

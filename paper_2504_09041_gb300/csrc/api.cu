@@ -286,7 +286,7 @@ int plan_box(int lattice, int nx, int ny, int nz, double Ra, double Pr, double M
     hc.gaxis = bc->gravity_axis;
     hc.fp16_sr = 1;
     hc.adj_sync = 2;   // adjoint step: 128 x 2 blocks with phase barriers (measured fastest)
-    hc.rows3d = 2;     // 3D FP32 / FP16S step: two rows per thread (measured +2 % FP32, +0.7 % FP16S)
+    hc.rows3d = 0;     // 3D FP32 / FP16S step: rows per thread chosen per form (rows3d_for)
     const double om_nu = 1.0 / (3.0 * P->nu + 0.5);
     const double om_alpha = 1.0 / (3.0 * P->alpha + 0.5);
     // App. A, B, C: shear / diffusivity rates from nu / alpha, bulk and every free rate 1
@@ -463,7 +463,8 @@ int lbm_set_param(lbm_handle h, const char* key, double v)
         return LBM_OK;
     }
     if (k == "rows3d") {
-        if (!(v == 1.0 || v == 2.0 || v == 4.0)) return fail(h, LBM_EINVAL, "rows3d must be 1, 2 or 4");
+        if (!(v == 0.0 || v == 1.0 || v == 2.0 || v == 4.0))
+            return fail(h, LBM_EINVAL, "rows3d must be 0 (automatic), 1, 2 or 4");
         h->hc.rows3d = (int)v;
         return LBM_OK;
     }

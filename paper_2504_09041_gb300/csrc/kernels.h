@@ -34,7 +34,7 @@ struct HostCoeffs {
     int gopt;   // energy attractors of orders 3-4: 0 = option A, 1 = option B
     int fp16_sr;   // F16S storage: stochastic (1) or nearest (0) rounding of stored deviations
     int index64;   // 1: the step uses 64-bit element offsets even where 32-bit ones suffice
-    int rows3d;    // 3D FP32 / FP16S step: rows of its column each thread updates (1 or 2)
+    int rows3d;    // 3D FP32 / FP16S step: rows of its column each thread updates (1, 2 or 4; 0 automatic)
     int adj_sync;  // adjoint step blocks: 0 = 64x2; with phase barriers 1 = 64x4, 2 = 128x2 (default),
                    // 3 = 32x4, 4 = 64x2
 };
@@ -194,6 +194,16 @@ inline int rate_class(const HostCoeffs& h)
 {
     if (!unit_energy_rates(h)) return 0;
     return unit_flow_rates(h) ? 2 : 1;
+}
+
+// Rows per thread of the 3D FP32 / FP16S step: the handle's setting, or when that is 0 the faster
+// one measured on the 256^3 cavity: one for FP16S storage with the reduced collisions of the
+// default rates (+0.8 % against two), two otherwise (FP32 +1.2 % at its 72 registers; FP16S with
+// the general collision +0.5-0.9 %).
+inline int rows3d_for(const HostCoeffs& h, bool f16s)
+{
+    if (h.rows3d > 0) return h.rows3d;
+    return f16s && rate_class(h) == 2 ? 1 : 2;
 }
 
 inline dim3 grid_shape(const Geometry& g, dim3 b)

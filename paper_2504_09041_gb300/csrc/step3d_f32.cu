@@ -19,12 +19,13 @@ static cudaError_t launch_plain_f32(const void* fin, const void* gin, void* fout
     using R = typename S::R;
     const dim3 b = block_shape(geo.nx, block, 3);
     const auto c = make_coeffs<R, 27, 15>(hc);
-    if (step_index32(geo, 27, hc) && hc.rows3d == 2) {
+    const int rows = rows3d_for(hc, false);
+    if (step_index32(geo, 27, hc) && rows == 2) {
         dim3 g = grid_shape(geo, b);
         g.y = (g.y + 1) / 2;
         step_d3q27_kernel<S, unsigned, 2, kU><<<g, b, 0, st>>>(
             (const T*)fin, (const T*)gin, (T*)fout, (T*)gout, geo, c, status);
-    } else if (step_index32(geo, 27, hc) && hc.rows3d == 4) {
+    } else if (step_index32(geo, 27, hc) && rows == 4) {
         dim3 g = grid_shape(geo, b);
         g.y = (g.y + 3) / 4;
         step_d3q27_kernel<S, unsigned, 4, kU><<<g, b, 0, st>>>(
