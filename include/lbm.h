@@ -176,8 +176,10 @@ LBM_API int lbm_sync(lbm_handle h);
 
 /*
  * Macroscopic fields of the streamed populations at the current time (App. A Step 7 and App. B/C
- * Step 7): rho, u (with the half-force term) and T, FP64, n = nx*ny*nz values each.  Pointers are
- * device pointers when device_ptrs != 0, else host pointers; any pointer may be NULL.
+ * Step 7): rho, u (with the half-force term) and T, FP64, n = nx*ny*nz values each.  The sums over
+ * the links run in the register type of the storage (FP32 for FP32 and FP16 storage) and are
+ * promoted to FP64.  Pointers are device pointers when device_ptrs != 0, else host pointers; any
+ * pointer may be NULL, and only the requested fields are computed and copied.
  */
 LBM_API int lbm_fields(lbm_handle h, double* rho, double* ux, double* uy, double* uz, double* T,
                int device_ptrs);

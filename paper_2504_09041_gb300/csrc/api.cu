@@ -632,20 +632,25 @@ int lbm_fields(lbm_handle h, double* rho, double* ux, double* uy, double* uz, do
     if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
     const size_t n = (size_t)h->geo.n;
     double* outs[5] = {rho, ux, uy, uz, T};
-    const bool direct = device_ptrs && rho && ux && uy && uz && T;
-    if (direct) {
+    if (device_ptrs) {   // the kernel writes the requested fields in place and skips the others
         LBM_CK(h, lbm::launch_fields(h->dim, h->prec, h->f[h->cur], h->g[h->cur], h->geo, h->hc, rho,
                                      ux, uy, uz, T, h->stream));
         return LBM_OK;
     }
-    Tmp tmp(h, 5 * n);
+    // host outputs: stage only the requested fields on the device
+    int k_req = 0;
+    for (int k = 0; k < 5; ++k) k_req += outs[k] != nullptr;
+    if (k_req == 0) return LBM_OK;
+    Tmp tmp(h, (size_t)k_req * n);
     if (!tmp.p) return fail(h, LBM_ENOMEM, "no device memory for the field staging buffer");
-    LBM_CK(h, lbm::launch_fields(h->dim, h->prec, h->f[h->cur], h->g[h->cur], h->geo, h->hc, tmp.p,
-                                 tmp.p + n, tmp.p + 2 * n, tmp.p + 3 * n, tmp.p + 4 * n, h->stream));
+    double* dev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0, m = 0; k < 5; ++k)
+        if (outs[k]) dev[k] = tmp.p + (size_t)(m++) * n;
+    LBM_CK(h, lbm::launch_fields(h->dim, h->prec, h->f[h->cur], h->g[h->cur], h->geo, h->hc, dev[0],
+                                 dev[1], dev[2], dev[3], dev[4], h->stream));
     for (int k = 0; k < 5; ++k)
         if (outs[k])
-            LBM_CK(h, cudaMemcpyAsync(outs[k], tmp.p + k * n, n * sizeof(double),
-                                      device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+            LBM_CK(h, cudaMemcpyAsync(outs[k], dev[k], n * sizeof(double), cudaMemcpyDeviceToHost,
                                       h->stream));
     LBM_CK(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;

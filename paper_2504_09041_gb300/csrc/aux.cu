@@ -133,6 +133,18 @@ __device__ __forceinline__ void pulled(const typename S::T* f, const typename S:
     }
 }
 
+// Lattice velocity component d of link a.
+template <int DIM>
+__host__ __device__ constexpr int ev(int a, int d)
+{
+    if constexpr (DIM == 2) return e9(a, d);
+    else return e27(a, d);
+}
+
+// rho, u and T at every node (App. A Step 7, App. B Step 7, Sec. 6.1 force); a null output is not
+// written.  The sums run over the pulled deviations in the storage's register type (FP32 for FP32
+// and FP16 storage, where an FP64 sum made this pass bound by the FP64 pipe) and are promoted to
+// FP64 for the outputs.
 template <class S, int DIM>
 __global__ void fields_kernel(const typename S::T* f, const typename S::T* g, Geometry geo,
                               HostCoeffs hc, double* rho, double* ux, double* uy, double* uz,
@@ -142,22 +154,29 @@ __global__ void fields_kernel(const typename S::T* f, const typename S::T* g, Ge
     using L = Lat<DIM>;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < geo.n;
          i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % geo.nx), y = (int)((i / geo.nx) % geo.ny), z = (int)(i / geo.nxy);
+        const int z = (int)(i / geo.nxy), rxy = (int)(i - (long long)z * geo.nxy);
+        const int y = rxy / geo.nx, x = rxy - y * geo.nx;
         R fo[L::QF], go[L::QG];
         pulled<S, DIM>(f, g, geo, R(hc.T_ref), x, y, z, fo, go);
-        double T = hc.T_ref, r = 1.0, j[3] = {0.0, 0.0, 0.0};
-        for (int b = 0; b < L::QG; ++b) T += (double)go[b];
-        for (int a = 0; a < L::QF; ++a) {
-            r += (double)fo[a];
-            for (int d = 0; d < DIM; ++d) j[d] += (double)fo[a] * (DIM == 2 ? e9(a, d) : e27(a, d));
-        }
+        R dT = go[0], drho = fo[0], j[3] = {R(0), R(0), R(0)};
+        static_for<L::QG - 1>([&](auto B) { dT += go[decltype(B)::value + 1]; });
+        static_for<L::QF - 1>([&](auto A) {
+            constexpr int a = decltype(A)::value + 1;
+            drho += fo[a];
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                if (ev<DIM>(a, d) == 1) j[d] += fo[a];
+                if (ev<DIM>(a, d) == -1) j[d] -= fo[a];
+            }
+        });
+        const double T = hc.T_ref + (double)dT, r = 1.0 + (double)drho;
         double F[3] = {0.0, 0.0, 0.0};
-        F[hc.gaxis] = hc.gbeta * (T - hc.T_ref);
-        rho[i] = r;
-        ux[i] = (j[0] + 0.5 * F[0]) / r;
-        uy[i] = (j[1] + 0.5 * F[1]) / r;
-        uz[i] = (j[2] + 0.5 * F[2]) / r;
-        Tout[i] = T;
+        F[hc.gaxis] = hc.gbeta * (double)dT;
+        if (rho) rho[i] = r;
+        if (ux) ux[i] = ((double)j[0] + 0.5 * F[0]) / r;
+        if (uy) uy[i] = ((double)j[1] + 0.5 * F[1]) / r;
+        if (uz) uz[i] = ((double)j[2] + 0.5 * F[2]) / r;
+        if (Tout) Tout[i] = T;
     }
 }
 
