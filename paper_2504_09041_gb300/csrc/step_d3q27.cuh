@@ -236,6 +236,65 @@ __device__ __forceinline__ void xraw_d3q27(const R f[27], R p[3][3][3])
         }
 }
 
+// Two lines of one sweep at once, with Blackwell's paired FP32 instructions (FADD2, FFMA2, FMUL2):
+// each lane performs exactly the operations of central_line / uncentral_line (a difference c - a
+// as the exact fused c + (-1) a).  The y and z sweeps pair the lines at x-orders 0 and 2.
+__device__ __forceinline__ void central_line2(float2& a, float2& b, float2& c, float u)
+{
+    const float2 m1 = make_float2(-1.0f, -1.0f), nu = make_float2(-u, -u);
+    const float2 k0 = __fadd2_rn(__fadd2_rn(a, b), c);
+    const float2 d = __ffma2_rn(m1, a, c);
+    const float2 s = __fadd2_rn(c, a);
+    const float2 k1 = __ffma2_rn(nu, k0, d);
+    const float2 k2 = __ffma2_rn(nu, __fadd2_rn(d, k1), s);
+    a = k0;
+    b = k1;
+    c = k2;
+}
+
+__device__ __forceinline__ void uncentral_line2(float2& a, float2& b, float2& c, float u)
+{
+    const float2 m1 = make_float2(-1.0f, -1.0f), u2 = make_float2(u, u), h = make_float2(0.5f, 0.5f);
+    const float2 k0 = a, k1 = b, k2 = c;
+    const float2 r1 = __ffma2_rn(u2, k0, k1);
+    const float2 r2 = __ffma2_rn(u2, __fadd2_rn(k1, r1), k2);
+    a = __fmul2_rn(h, __ffma2_rn(m1, r1, r2));
+    b = __ffma2_rn(m1, r2, k0);
+    c = __fmul2_rn(h, __fadd2_rn(r2, r1));
+}
+
+// One y or z sweep over the nine lines of p: axis 1 sweeps j (lines (k, a)), axis 2 sweeps k
+// (lines (j, a)); FP32 pairs the lines at a = 0 and a = 2.
+template <bool kInverse, int kAxis, class R>
+__device__ __forceinline__ void sweep_yz_d3q27(R p[3][3][3], R u)
+{
+#define LBM_P(l, m, a) (kAxis == 1 ? p[l][m][a] : p[m][l][a])
+    if constexpr (std::is_same<R, float>::value) {
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            float2 v0 = make_float2(LBM_P(l, 0, 0), LBM_P(l, 0, 2));
+            float2 v1 = make_float2(LBM_P(l, 1, 0), LBM_P(l, 1, 2));
+            float2 v2 = make_float2(LBM_P(l, 2, 0), LBM_P(l, 2, 2));
+            if constexpr (kInverse) uncentral_line2(v0, v1, v2, u);
+            else central_line2(v0, v1, v2, u);
+            LBM_P(l, 0, 0) = v0.x; LBM_P(l, 0, 2) = v0.y;
+            LBM_P(l, 1, 0) = v1.x; LBM_P(l, 1, 2) = v1.y;
+            LBM_P(l, 2, 0) = v2.x; LBM_P(l, 2, 2) = v2.y;
+            if constexpr (kInverse) uncentral_line(LBM_P(l, 0, 1), LBM_P(l, 1, 1), LBM_P(l, 2, 1), u);
+            else central_line(LBM_P(l, 0, 1), LBM_P(l, 1, 1), LBM_P(l, 2, 1), u);
+        }
+    } else {
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if constexpr (kInverse) uncentral_line(LBM_P(l, 0, a), LBM_P(l, 1, a), LBM_P(l, 2, a), u);
+                else central_line(LBM_P(l, 0, a), LBM_P(l, 1, a), LBM_P(l, 2, a), u);
+            }
+    }
+#undef LBM_P
+}
+
 // Central moments from the raw x-line values: the u part of the x sweep (the same operations as
 // central_line), then the y and z sweeps.
 template <class R>
@@ -250,14 +309,8 @@ __device__ __forceinline__ void central_from_xraw_d3q27(R p[3][3][3], R ux, R uy
             p[k][j][1] = k1;
             p[k][j][2] = s - ux * (d + k1);
         }
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) central_line(p[k][0][a], p[k][1][a], p[k][2][a], uy);
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) central_line(p[0][b][a], p[1][b][a], p[2][b][a], uz);
+    sweep_yz_d3q27<false, 1>(p, uy);
+    sweep_yz_d3q27<false, 2>(p, uz);
 }
 
 // Inverse transform; the populations come out multiplied by 2^L (L = 0 except for FP16 storage,
@@ -265,14 +318,8 @@ __device__ __forceinline__ void central_from_xraw_d3q27(R p[3][3][3], R ux, R uy
 template <int L = 0, class R>
 __device__ __forceinline__ void from_central_d3q27(R p[3][3][3], R f[27], R ux, R uy, R uz)
 {
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) uncentral_line(p[0][b][a], p[1][b][a], p[2][b][a], uz);
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) uncentral_line(p[k][0][a], p[k][1][a], p[k][2][a], uy);
+    sweep_yz_d3q27<true, 2>(p, uz);
+    sweep_yz_d3q27<true, 1>(p, uy);
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
