@@ -114,4 +114,31 @@ __device__ __forceinline__ void uncentral_line_pow2(R& a, R& b, R& c, R u)
     c = h * (r2 + r1);
 }
 
+// Two lines of one sweep at once, with Blackwell's paired FP32 instructions (FADD2, FFMA2, FMUL2):
+// each lane performs exactly the operations of central_line / uncentral_line (a difference c - a
+// as the exact fused c + (-1) a).  The sweeps that use them pair the lines at x-orders 0 and 2.
+__device__ __forceinline__ void central_line2(float2& a, float2& b, float2& c, float u)
+{
+    const float2 m1 = make_float2(-1.0f, -1.0f), nu = make_float2(-u, -u);
+    const float2 k0 = __fadd2_rn(__fadd2_rn(a, b), c);
+    const float2 d = __ffma2_rn(m1, a, c);
+    const float2 s = __fadd2_rn(c, a);
+    const float2 k1 = __ffma2_rn(nu, k0, d);
+    const float2 k2 = __ffma2_rn(nu, __fadd2_rn(d, k1), s);
+    a = k0;
+    b = k1;
+    c = k2;
+}
+
+__device__ __forceinline__ void uncentral_line2(float2& a, float2& b, float2& c, float u)
+{
+    const float2 m1 = make_float2(-1.0f, -1.0f), u2 = make_float2(u, u), h = make_float2(0.5f, 0.5f);
+    const float2 k0 = a, k1 = b, k2 = c;
+    const float2 r1 = __ffma2_rn(u2, k0, k1);
+    const float2 r2 = __ffma2_rn(u2, __fadd2_rn(k1, r1), k2);
+    a = __fmul2_rn(h, __ffma2_rn(m1, r1, r2));
+    b = __ffma2_rn(m1, r2, k0);
+    c = __fmul2_rn(h, __fadd2_rn(r2, r1));
+}
+
 }  // namespace lbm
