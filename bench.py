@@ -272,18 +272,24 @@ def run_gpu(args):
     launches = args.steps + 2
 
     # end to end through the C ABI with host buffers: upload a state from pinned host memory,
-    # run the steps, read back the wall Nusselt numbers and the temperature field.
+    # run the steps, read back the wall Nusselt numbers and the temperature field.  One untimed
+    # pass of the same job first (as the steps have their warm-up), then the timed pass.
     state_host = torch.empty(info.state_bytes, dtype=torch.uint8).pin_memory()
     T_host = torch.empty(n, dtype=torch.float64).pin_memory()
     L.lbm_get_state(lat.h, state_host.numpy())
+
+    def e2e_job(k):
+        L.lbm_set_state(lat.h, state_host.numpy())
+        L.lbm_step(lat.h, k)
+        L.lbm_nusselt(lat.h, hot)
+        L.lbm_nusselt(lat.h, cold)
+        L.lbm_fields(lat.h, None, None, None, None, T_host.data_ptr(), 0)
+
+    e2e_job(args.steps)
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    L.lbm_set_state(lat.h, state_host.numpy())
-    L.lbm_step(lat.h, args.steps)
-    L.lbm_nusselt(lat.h, hot)
-    L.lbm_nusselt(lat.h, cold)
-    L.lbm_fields(lat.h, None, None, None, None, T_host.data_ptr(), 0)
+    e2e_job(args.steps)
     torch.cuda.synchronize()
     t_e2e = reduce_max(time.perf_counter() - t0, world)
 
